@@ -1,0 +1,55 @@
+"""Build and load the oracle's plain-C loops (quapi_oracle.c).  Test infrastructure only."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "quapi_oracle.c")
+_LIB = os.path.join(_HERE, "libquapi_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile quapi_oracle.c with gcc (-O2, OpenMP) into oracle/libquapi_oracle.so."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            for name in ("oracle_grow", "oracle_step", "oracle_readout"):
+                fn = getattr(L, name)
+                fn.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+                fn.restype = None
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.complex128 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def call(name: str, M2: int, n: int, A: np.ndarray, G: np.ndarray, g: np.ndarray, out: np.ndarray):
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    G = np.ascontiguousarray(G, dtype=np.complex128)
+    g = np.ascontiguousarray(g, dtype=np.complex128)
+    getattr(lib(), name)(M2, n, _ptr(A), _ptr(G), _ptr(g), _ptr(out))
+    return out
