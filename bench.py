@@ -1,0 +1,345 @@
+"""Benchmark of the QUAPI tensor propagator on one GB300 (or N replicas under torchrun).
+
+One bench step = one complete propagation of the large memory-bound spin-boson
+workload (M=2, Delta k_max=14: 4^14 = 268,435,456 tensor entries; Ohmic alpha=0.5,
+wc=2.5, beta=0.5, dt=0.15, 1000 steps, rho read out at the final step only):
+growth phase, 987 fused steady-state steps, the final readout.
+
+Metric: tensor element-updates/s = (M^2)^L entries x (N - L + 1) full-tensor
+passes / time.  value: FP32 form, tables and rho0 resident on the device
+(quapi_propagate_device); e2e: the public host API per step (quapi_setup from
+host arrays + quapi_propagate to host rho + quapi_destroy).  forms.fp64: the
+plain FP64 form on the same workload.  roofline: the dominant kernel (the
+fused steady-state step) timed alone with CUDA events on its stream.
+
+--impl reference: the FP64 CPU oracle on the host cores, a bounded sample of
+the same workload per step (a few steady-state steps on a full-size tensor).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QUAPI tensor element-updates/s (M=2, dkmax=14; FP32 form, FP64 form in forms.fp64)"
+UNIT = "element-updates/s"
+WORKLOAD = "spin_boson_L14"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_key):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    src = os.path.join(ROOT, "paper_1205_6872_gb300", "csrc", "propagate.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key:
+                    if parts[2] == sha:
+                        return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+def dist_setup():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def element_updates(p):
+    return float((p.M * p.M) ** p.L) * float(p.N - p.L + 1)
+
+
+def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None):
+    opts = q.quapi_opts_init(precision=precision, cuda_stream=stream)
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, opts)
+    try:
+        rho0 = torch.tensor(np.asarray(p.rho0).reshape(-1), dtype=torch.complex128, device="cuda")
+        rho = torch.empty(p.M * p.M, dtype=torch.complex128, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                q.quapi_propagate_device(ctx, rho0, [p.N], rho)
+        stream.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        l0 = q.quapi_kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            q.quapi_propagate_device(ctx, rho0, [p.N], rho)
+        e1.record(stream)
+        e1.synchronize()
+        launches = q.quapi_kernel_launches() - l0
+        clocks = sampler.stop() if sampler else None
+        barrier(world)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ms = max_over_ranks(ms, world)
+        rho_final = rho.cpu().numpy().reshape(p.M, p.M)
+        # dominant kernel alone: the fused steady-state step on a full tensor
+        n_el = (p.M * p.M) ** p.L
+        dt_ = torch.complex64 if precision == 32 else torch.complex128
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        A = torch.randn(n_el, dtype=dt_, device="cuda", generator=gen)
+        B = torch.empty_like(A)
+        reps = 20
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                q.quapi_step_device(ctx, p.L + 1, A, B, None)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for r in range(reps):
+            src, dst = (A, B) if r % 2 == 0 else (B, A)
+            q.quapi_step_device(ctx, p.L + 1, src, dst, None)
+        k1.record(stream)
+        k1.synchronize()
+        kern_ms = k0.elapsed_time(k1) / reps
+        del A, B
+        torch.cuda.empty_cache()
+    finally:
+        q.quapi_destroy(ctx)
+    return dict(ms=ms, launches=launches, clocks=clocks, rho=rho_final, kernel_ms=kern_ms)
+
+
+def time_e2e(q, torch, p, precision, steps, warmup):
+    """Public host API per step: setup from host arrays, propagate to host rho, destroy."""
+    def one():
+        ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                            q.quapi_opts_init(precision=precision))
+        try:
+            return q.quapi_propagate(ctx, p.rho0, [p.N], p.M)
+        finally:
+            q.quapi_destroy(ctx)
+    for _ in range(max(1, warmup)):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps
+
+
+def cpu_oracle_sample(p, nsteps):
+    """The FP64 oracle's steady-state step on a full-size tensor, nsteps times (host cores)."""
+    import oracle
+    import oracle.recurrence as rec
+    from oracle.eta import Spectral
+    from paper_1205_6872_gb300 import workloads as wl
+    run = oracle.OracleRun(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L)
+    G, g, n_in, summed = rec.step_tables(run.eta, p.s, run.K, p.L, p.L + 1)
+    A = wl.random_tensor((p.M * p.M) ** p.L, seed=11)
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        A = rec.apply_step(A, G, g, n_in, summed)
+    dt = time.perf_counter() - t0
+    return dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_1205_6872_gb300 import workloads as wl
+    p = wl.spin_boson_L14()
+    per_step = 2  # steady-state steps of the full-size tensor per bench step
+    for _ in range(args.warmup):
+        cpu_oracle_sample(p, 1)
+    t = [cpu_oracle_sample(p, per_step) for _ in range(args.steps)]
+    ms = 1000.0 * sum(t) / len(t)
+    ups = per_step * float((p.M * p.M) ** p.L) / (ms / 1000.0)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{per_step} steady-state steps of the 4^14-entry tensor per bench step (FP64 oracle, OpenMP)"
+    line = dict(metric=METRIC, value=ups, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, sample=sample),
+                cpu_baseline=dict(value=ups, unit=UNIT, cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=ups, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1205_6872_gb300 import quapi as q
+    from paper_1205_6872_gb300 import workloads as wl
+    q.load()
+    p = wl.spin_boson_L14()
+    stream = torch.cuda.Stream()
+    sampler = ClockSampler(local)
+    r32 = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, sampler)
+    ups = element_updates(p)
+    value = world * ups / (r32["ms"] / 1000.0)
+    forms = {}
+    if not args.no_fp64:
+        r64 = time_form(q, torch, p, q.QUAPI_FP64, args.steps, args.warmup, stream, world)
+        forms["fp64"] = dict(value=world * ups / (r64["ms"] / 1000.0), unit=UNIT, ms_per_step=r64["ms"],
+                             kernel_ms=r64["kernel_ms"], rho_final=[[float(z.real), float(z.imag)]
+                                                                    for z in r64["rho"].reshape(-1)])
+        forms["fp64"]["fp32_vs_fp64_max_abs"] = float(np.abs(r32["rho"] - r64["rho"]).max())
+        forms["fp64"]["speedup_fp32_over_fp64"] = r64["ms"] / r32["ms"]
+    e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1))
+    e2e_s = max_over_ranks(e2e_s, world)
+    peak, peak_kind = measured_peaks()
+    bytes_per_launch = 16.0 * (p.M * p.M) ** p.L  # FP32: 8 B read + 8 B written per entry
+    achieved = bytes_per_launch / (r32["kernel_ms"] / 1000.0) / 1e9
+    traffic = recorded_traffic("step_kernel_fp32_m2")
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=r32["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, form="fp32", readout="justFinalPoint",
+                    parallelism=f"replicas{world}",
+                    l2="inputs larger than L2: each step streams two 2.1 GB tensors"),
+        roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                      traffic=traffic, peak_source=peak_kind, kernel="step_kernel<M=2,FP32>",
+                      kernel_ms=r32["kernel_ms"], algorithmic_bytes_per_launch=bytes_per_launch),
+        e2e=dict(value=world * ups / e2e_s, unit=UNIT, seconds_per_step=e2e_s,
+                 h2d_bytes_per_step=8 * p.M + 16 * p.M * p.M * 2, d2h_bytes_per_step=16 * p.M * p.M),
+        gpu_launches=int(r32["launches"]),
+        clocks=r32["clocks"],
+        forms=forms,
+        rho_final=[[float(z.real), float(z.imag)] for z in r32["rho"].reshape(-1)],
+    )
+    if rank == 0 and world == 1 and not args.no_cpu:
+        nst = 2
+        t = cpu_oracle_sample(p, nst)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line["cpu_baseline"] = dict(value=nst * float((p.M * p.M) ** p.L) / t, unit=UNIT, cores=cores,
+                                    kind="oracle",
+                                    sample=f"{nst} steady-state steps of the 4^14-entry tensor (FP64 oracle)")
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -16,7 +16,7 @@ What it computes (all FP64, hbar = k_B = 1):
 * ``system``     -- the bare system propagator e^{-i H dt} and the
   forward/backward pair propagator K(x', x) of the path-integral expression
   for <s_N^+|rho(t)|s_N^-> (Sec. II).
-* ``propagate``  -- the tensor-propagator recurrence (Sec. I, Makri-Makarov
+* ``recurrence`` -- the tensor-propagator recurrence (Sec. I, Makri-Makarov
   scheme; memory length Delta k_max, Sec. II) written plainly: growth of the
   augmented tensor A for k < Delta k_max, then multiply-by-T and sum over the
   oldest path index, and the rho readout at the requested steps
@@ -35,5 +35,5 @@ large memory length (no closed form exists and the paper prints no rho values).
 
 from .eta import Spectral, eta_boxes, eta_table, pack_eta, unpack_eta, strang_box  # noqa: F401
 from .system import propagator_U, pair_propagator_K, coupling_d  # noqa: F401
-from .propagate import propagate, step_tables, readout_tables, OracleRun  # noqa: F401
+from .recurrence import propagate, step_tables, readout_tables, OracleRun  # noqa: F401
 from .bruteforce import rho_bruteforce  # noqa: F401

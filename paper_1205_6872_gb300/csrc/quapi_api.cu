@@ -1,0 +1,603 @@
+// Host side of libquapi.so: argument checks, the step planner (which eta
+// coefficient joins which pair of path points), device memory, and the C ABI
+// entry points declared in include/quapi.h.
+//
+// Path bookkeeping (Sec. II, truncated influence functional; Sec. I, tensor
+// propagator scheme).  The tensor A_{n-1} that feeds the step adding path
+// point n holds n_in = min(n, L) points; input digit p holds point
+// n - n_in + p.  The new point pairs with each stored point at distance
+// dk = n - point <= L:
+//   growth / step tensor (new point propagates on as an interior point):
+//     point 0 -> eta_{n0} (Eq. etaK0generalStrang), otherwise interior eta_dk,
+//     self term interior eta_0;
+//   readout of rho(t_n) (STRANG end point, Eqs. etaNNgeneralStrang,
+//   etaNkgeneralStrang, etaN0generalStrang):
+//     point 0 -> eta_{n0}^{end}, otherwise eta_{n,n-dk}^{end}, self eta_NN.
+// Once n >= L the oldest stored point is summed (it leaves the memory window).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "quapi_internal.h"
+
+using namespace quapi;
+
+namespace quapi {
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace quapi
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+// indices into the 4L+3 eta vector (layout documented in quapi.h)
+inline int eta_interior(int L, int dk) { (void)L; return dk; }
+inline int eta_point0(int L, int k) { return L + 1 + (k - 1); }
+inline int eta_end_self(int L) { return 2 * L + 1; }
+inline int eta_end(int L, int dk) { return 2 * L + 2 + (dk - 1); }
+inline int eta_end_point0(int L, int N) { return 3 * L + 2 + (N - 1); }
+inline int eta_self0(int L) { return 4 * L + 2; }
+
+int64_t ipow(int64_t b, int e) {
+    int64_t r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+int max_dkmax(int M) { return M == 2 ? 16 : 10; }
+int lo_digits_max(int M) { return M == 2 ? 4 : 2; }
+
+}  // namespace
+
+struct quapi_ctx {
+    int M = 0, M2 = 0, L = 0, form = QUAPI_FP64, endpoint = QUAPI_ENDPOINT_STRANG;
+    double dt = 0.0;
+    cudaStream_t st = nullptr;
+    double* d_s = nullptr;
+    double2 *d_H = nullptr, *d_U = nullptr, *d_K = nullptr, *d_eta = nullptr, *d_rho0 = nullptr;
+    double2* d_slots = nullptr;
+    size_t slots_cap = 0;
+    void* buf[2] = {nullptr, nullptr};
+    bool own_buf = true;
+    unsigned char* d_tables = nullptr;
+    double2* d_partial = nullptr;
+    int max_grid = 0;
+    std::vector<OpPlan> grow_ops;   // index n = 1..L-1
+    std::vector<OpPlan> read_ops;   // index N = 1..L
+    OpPlan step_first, step_steady, read_steady;
+    std::string err;
+    std::vector<double> host_s;
+};
+
+namespace {
+
+quapi_status fail(quapi_ctx* c, quapi_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    g_thread_error = msg;
+    return st;
+}
+
+quapi_status cuda_fail(quapi_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? QUAPI_ERR_OOM : QUAPI_ERR_CUDA, m);
+}
+
+#define QCHECK(c, call, what)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, (what)); \
+    } while (0)
+
+size_t elem_bytes(int form) { return form == QUAPI_FP64 ? 16 : 8; }
+
+// Plan of one operation on an input tensor of n_in digits.
+OpPlan make_plan(int M, int kind, int n_in, bool summed, const int* eta_idx, int self_idx) {
+    OpPlan p;
+    p.kind = kind;
+    p.n_in = n_in;
+    p.summed = summed ? 1 : 0;
+    p.nk = n_in - p.summed;
+    p.j = std::min(p.nk, lo_digits_max(M));
+    p.lo_size = ipow(M * M, p.j);
+    p.hi_size = ipow(M * M, p.nk - p.j);
+    for (int q = 0; q < n_in; ++q) p.eta_idx[q] = eta_idx[q];
+    p.self_idx = self_idx;
+    return p;
+}
+
+OpPlan plan_step(int M, int L, int64_t n) {
+    int n_in = (int)std::min<int64_t>(n, L);
+    int idx[kMaxDigits];
+    for (int p = 0; p < n_in; ++p) {
+        int64_t point = n - n_in + p;
+        int dk = (int)(n - point);
+        idx[p] = (point == 0) ? eta_point0(L, (int)n) : eta_interior(L, dk);
+    }
+    bool summed = n >= L;
+    return make_plan(M, summed ? OP_STEP : OP_GROW, n_in, summed, idx, eta_interior(L, 0));
+}
+
+OpPlan plan_readout(int M, int L, int64_t N, int endpoint) {
+    int n_in = (int)std::min<int64_t>(N, L);
+    int idx[kMaxDigits];
+    for (int p = 0; p < n_in; ++p) {
+        int64_t point = N - n_in + p;
+        int dk = (int)(N - point);
+        if (endpoint == QUAPI_ENDPOINT_STRANG)
+            idx[p] = (point == 0) ? eta_end_point0(L, (int)N) : eta_end(L, dk);
+        else
+            idx[p] = (point == 0) ? eta_point0(L, (int)N) : eta_interior(L, dk);
+    }
+    int self = endpoint == QUAPI_ENDPOINT_STRANG ? eta_end_self(L) : eta_interior(L, 0);
+    return make_plan(M, OP_READ, n_in, true, idx, self);
+}
+
+size_t plan_bytes(const OpPlan& p, int M2) {
+    const size_t e = 16;  // double2 or ff2
+    size_t b = 0;
+    if (p.summed) b += (size_t)M2 * M2 * e;
+    b += (size_t)M2 * p.lo_size * e;
+    b += (size_t)M2 * p.hi_size * e;
+    return b;
+}
+
+void assign_offsets(OpPlan& p, int M2, size_t& cursor) {
+    const size_t e = 16;
+    auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    cursor = align(cursor);
+    p.off_isum = cursor;
+    if (p.summed) cursor += (size_t)M2 * M2 * e;
+    cursor = align(cursor);
+    p.off_lo = cursor;
+    cursor += (size_t)M2 * p.lo_size * e;
+    cursor = align(cursor);
+    p.off_hi = cursor;
+    cursor += (size_t)M2 * p.hi_size * e;
+}
+
+// every table set the context needs, in a fixed order
+std::vector<OpPlan*> all_plans(quapi_ctx* c) {
+    std::vector<OpPlan*> v;
+    for (int n = 1; n < c->L; ++n) v.push_back(&c->grow_ops[n]);
+    for (int N = 1; N <= c->L; ++N) v.push_back(&c->read_ops[N]);
+    v.push_back(&c->step_first);
+    v.push_back(&c->step_steady);
+    v.push_back(&c->read_steady);
+    return v;
+}
+
+void make_all_plans(quapi_ctx* c) {
+    c->grow_ops.assign(c->L + 1, OpPlan());
+    c->read_ops.assign(c->L + 1, OpPlan());
+    for (int n = 1; n < c->L; ++n) c->grow_ops[n] = plan_step(c->M, c->L, n);
+    for (int N = 1; N <= c->L; ++N) c->read_ops[N] = plan_readout(c->M, c->L, N, c->endpoint);
+    c->step_first = plan_step(c->M, c->L, c->L);
+    c->step_steady = plan_step(c->M, c->L, c->L + 1);
+    c->read_steady = plan_readout(c->M, c->L, c->L + 1, c->endpoint);
+}
+
+size_t tables_bytes_for(int M, int L, int endpoint) {
+    quapi_ctx tmp;
+    tmp.M = M;
+    tmp.M2 = M * M;
+    tmp.L = L;
+    tmp.endpoint = endpoint;
+    make_all_plans(&tmp);
+    size_t cursor = 0;
+    for (OpPlan* p : all_plans(&tmp)) assign_offsets(*p, tmp.M2, cursor);
+    return cursor + 256;
+}
+
+quapi_status check_common(const double* s, int M, const double* H, double dt, int L, const quapi_opts* o) {
+    if (!s || !H) return fail(nullptr, QUAPI_ERR_ARG, "s and H must not be NULL");
+    if (M != 2 && M != 3) return fail(nullptr, QUAPI_ERR_ARG, "M must be 2 or 3");
+    if (L < 1 || L > max_dkmax(M)) return fail(nullptr, QUAPI_ERR_ARG, "dkmax out of range (1..16 for M=2, 1..10 for M=3)");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, QUAPI_ERR_ARG, "dt must be > 0");
+    for (int i = 0; i < M; ++i)
+        if (!std::isfinite(s[i])) return fail(nullptr, QUAPI_ERR_ARG, "s must be finite");
+    for (int r = 0; r < M; ++r)
+        for (int q = 0; q < M; ++q) {
+            double ar = H[2 * (r * M + q)], ai = H[2 * (r * M + q) + 1];
+            double br = H[2 * (q * M + r)], bi = H[2 * (q * M + r) + 1];
+            if (!std::isfinite(ar) || !std::isfinite(ai)) return fail(nullptr, QUAPI_ERR_ARG, "H must be finite");
+            if (std::fabs(ar - br) > 1e-12 || std::fabs(ai + bi) > 1e-12)
+                return fail(nullptr, QUAPI_ERR_ARG, "H must be Hermitian (tolerance 1e-12)");
+        }
+    if (o) {
+        if (o->precision != QUAPI_FP64 && o->precision != QUAPI_FP32)
+            return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64 or QUAPI_FP32");
+        if (o->endpoint_mode != QUAPI_ENDPOINT_STRANG && o->endpoint_mode != QUAPI_ENDPOINT_INTERIOR)
+            return fail(nullptr, QUAPI_ERR_ARG, "unknown endpoint_mode");
+    }
+    return QUAPI_OK;
+}
+
+// Allocation, eta (given or by quadrature), propagators and tables.
+quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spectral* J, double beta,
+                        const double* eta_host, double dt, int L, const quapi_opts* opts, quapi_ctx** out) {
+    if (!out) return fail(nullptr, QUAPI_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    quapi_opts o;
+    quapi_opts_init(&o);
+    if (opts) o = *opts;
+    quapi_status stc = check_common(s, M, H, dt, L, &o);
+    if (stc != QUAPI_OK) return stc;
+    if (!eta_host) {
+        if (!J) return fail(nullptr, QUAPI_ERR_ARG, "J must not be NULL");
+        if (J->kind != QUAPI_J_OHMIC_EXP && J->kind != QUAPI_J_SUPEROHMIC_GAUSS)
+            return fail(nullptr, QUAPI_ERR_ARG, "unknown spectral density kind");
+        if (!(J->a >= 0.0) || !(J->wc > 0.0) || !std::isfinite(J->a) || !std::isfinite(J->wc))
+            return fail(nullptr, QUAPI_ERR_ARG, "spectral density needs a >= 0 and wc > 0");
+        if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, QUAPI_ERR_ARG, "beta must be > 0");
+    }
+    const int M2 = M * M;
+    const int64_t nelem = ipow(M2, L);
+    const size_t tensor_bytes = 2 * (size_t)nelem * elem_bytes(o.precision);
+    if (o.workspace && o.workspace_bytes < tensor_bytes)
+        return fail(nullptr, QUAPI_ERR_OOM, "caller workspace smaller than the two tensors");
+
+    quapi_ctx* c = new quapi_ctx();
+    c->M = M;
+    c->M2 = M2;
+    c->L = L;
+    c->dt = dt;
+    c->form = o.precision;
+    c->endpoint = o.endpoint_mode;
+    c->st = reinterpret_cast<cudaStream_t>(o.cuda_stream);
+    c->host_s.assign(s, s + M);
+    auto bail = [&](quapi_status st) {
+        std::string m = c->err;
+        quapi_destroy(c);
+        g_thread_error = m;
+        return st;
+    };
+#define SCHECK(call, what)                                            \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return bail(cuda_fail(c, e_, (what))); \
+    } while (0)
+
+    const int neta = 4 * L + 3;
+    SCHECK(cudaMalloc(&c->d_s, sizeof(double) * M), "cudaMalloc(s)");
+    SCHECK(cudaMalloc(&c->d_H, sizeof(double2) * M * M), "cudaMalloc(H)");
+    SCHECK(cudaMalloc(&c->d_U, sizeof(double2) * M * M), "cudaMalloc(U)");
+    SCHECK(cudaMalloc(&c->d_K, sizeof(double2) * M2 * M2), "cudaMalloc(K)");
+    SCHECK(cudaMalloc(&c->d_eta, sizeof(double2) * neta), "cudaMalloc(eta)");
+    SCHECK(cudaMalloc(&c->d_rho0, sizeof(double2) * M2), "cudaMalloc(rho0)");
+    if (o.workspace) {
+        c->own_buf = false;
+        c->buf[0] = o.workspace;
+        c->buf[1] = static_cast<unsigned char*>(o.workspace) + tensor_bytes / 2;
+    } else {
+        SCHECK(cudaMalloc(&c->buf[0], tensor_bytes / 2), "cudaMalloc(tensor A)");
+        SCHECK(cudaMalloc(&c->buf[1], tensor_bytes / 2), "cudaMalloc(tensor B)");
+    }
+    make_all_plans(c);
+    size_t cursor = 0;
+    for (OpPlan* p : all_plans(c)) assign_offsets(*p, M2, cursor);
+    SCHECK(cudaMalloc(&c->d_tables, cursor + 256), "cudaMalloc(tables)");
+    c->max_grid = num_sms() * 8;  // at most 8 resident CTAs of 256 threads per SM
+    SCHECK(cudaMalloc(&c->d_partial, sizeof(double2) * M2 * (size_t)c->max_grid), "cudaMalloc(partials)");
+
+    SCHECK(cudaMemcpyAsync(c->d_s, s, sizeof(double) * M, cudaMemcpyHostToDevice, c->st), "copy s");
+    SCHECK(cudaMemcpyAsync(c->d_H, H, sizeof(double2) * M * M, cudaMemcpyHostToDevice, c->st), "copy H");
+    SCHECK(launch_propagator(c->d_H, M, dt, c->d_U, c->d_K, c->st), "propagator kernel");
+
+    EtaJob* d_jobs = nullptr;
+    double* d_gl = nullptr;
+    if (eta_host) {
+        SCHECK(cudaMemcpyAsync(c->d_eta, eta_host, sizeof(double2) * neta, cudaMemcpyHostToDevice, c->st),
+               "copy eta");
+    } else {
+        // box geometry of every eta (symmetric placement): point 0 owns [0, dt/2],
+        // interior point k owns [(k-1/2)dt, (k+1/2)dt], the end point N owns [(N-1/2)dt, N dt]
+        std::vector<EtaJob> jobs(neta);
+        auto self = [](double w) { return EtaJob{w, -1.0, 0.0}; };
+        auto pair = [](double w1, double w2, double D) { return EtaJob{w1, w2, D}; };
+        jobs[eta_interior(L, 0)] = self(dt);
+        for (int dk = 1; dk <= L; ++dk) jobs[eta_interior(L, dk)] = pair(dt, dt, dk * dt);
+        for (int k = 1; k <= L; ++k) jobs[eta_point0(L, k)] = pair(dt, 0.5 * dt, k * dt - 0.25 * dt);
+        jobs[eta_end_self(L)] = self(0.5 * dt);
+        for (int dk = 1; dk <= L; ++dk) jobs[eta_end(L, dk)] = pair(0.5 * dt, dt, dk * dt - 0.25 * dt);
+        for (int N = 1; N <= L; ++N) jobs[eta_end_point0(L, N)] = pair(0.5 * dt, 0.5 * dt, N * dt - 0.5 * dt);
+        jobs[eta_self0(L)] = self(0.5 * dt);
+        double kmax = 0.0;
+        for (const EtaJob& jb : jobs) kmax = std::max(kmax, jb.w2 < 0 ? jb.w1 : jb.D + 0.5 * (jb.w1 + jb.w2));
+        const double wmax = (J->kind == QUAPI_J_OHMIC_EXP) ? 46.0 * J->wc : 7.5 * J->wc;
+        int panels = (int)std::ceil(wmax * kmax / 2.0);
+        panels = std::max(panels, 256);
+        panels = std::min(panels, 1 << 16);
+        std::vector<double> gx, gw;
+        gauss_legendre_nodes(16, gx, gw);
+        std::vector<double> gl(gx);
+        gl.insert(gl.end(), gw.begin(), gw.end());
+        SCHECK(cudaMalloc(&d_jobs, sizeof(EtaJob) * neta), "cudaMalloc(eta jobs)");
+        SCHECK(cudaMalloc(&d_gl, sizeof(double) * gl.size()), "cudaMalloc(GL nodes)");
+        SCHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EtaJob) * neta, cudaMemcpyHostToDevice, c->st), "copy jobs");
+        SCHECK(cudaMemcpyAsync(d_gl, gl.data(), sizeof(double) * gl.size(), cudaMemcpyHostToDevice, c->st), "copy GL");
+        SCHECK(launch_eta_quadrature(d_jobs, neta, J->kind, J->a, J->wc, beta, panels, d_gl, 16, c->d_eta, c->st),
+               "eta quadrature kernel");
+    }
+
+    // factor tables of every operation, one launch
+    std::vector<OpPlan*> plans = all_plans(c);
+    std::vector<BuildDesc> descs(plans.size());
+    int64_t max_entries = 0;
+    for (size_t i = 0; i < plans.size(); ++i) {
+        const OpPlan& p = *plans[i];
+        BuildDesc& d = descs[i];
+        std::memset(&d, 0, sizeof(d));
+        d.M = M;
+        d.M2 = M2;
+        d.n_in = p.n_in;
+        d.summed = p.summed;
+        d.nk = p.nk;
+        d.j = p.j;
+        d.form = c->form;
+        for (int q = 0; q < p.n_in; ++q) d.eta_idx[q] = p.eta_idx[q];
+        d.self_idx = p.self_idx;
+        d.lo_size = p.lo_size;
+        d.hi_size = p.hi_size;
+        d.eta = c->d_eta;
+        d.s = c->d_s;
+        d.K = c->d_K;
+        d.isum = c->d_tables + p.off_isum;
+        d.lo = c->d_tables + p.off_lo;
+        d.hi = c->d_tables + p.off_hi;
+        int64_t ent = (p.summed ? M2 * M2 : 0) + M2 * p.lo_size + M2 * p.hi_size;
+        max_entries = std::max(max_entries, ent);
+    }
+    BuildDesc* d_descs = nullptr;
+    SCHECK(cudaMalloc(&d_descs, sizeof(BuildDesc) * descs.size()), "cudaMalloc(build descs)");
+    SCHECK(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BuildDesc) * descs.size(), cudaMemcpyHostToDevice, c->st),
+           "copy build descs");
+    SCHECK(launch_build_tables(d_descs, (int)descs.size(), M2, max_entries, c->st), "table build kernel");
+    SCHECK(cudaStreamSynchronize(c->st), "setup synchronize");
+    cudaFree(d_descs);
+    if (d_jobs) cudaFree(d_jobs);
+    if (d_gl) cudaFree(d_gl);
+#undef SCHECK
+    *out = c;
+    return QUAPI_OK;
+}
+
+// Readout on A_in (n_in digits) with plan rp, optionally fused with the step plan sp.
+quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const void* A_in, void* A_out,
+                         double2* rho_slot) {
+    const int64_t F = ipow(c->M2, (sp ? sp->n_in : rp->n_in) - 1);
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.A_in = A_in;
+    a.A_out = A_out;
+    a.F = F;
+    const OpPlan* ref = sp ? sp : rp;
+    if (sp) {
+        a.isum = c->d_tables + sp->off_isum;
+        a.lo = c->d_tables + sp->off_lo;
+        a.hi = c->d_tables + sp->off_hi;
+    }
+    if (rp) {
+        a.isum_e = c->d_tables + rp->off_isum;
+        a.lo_e = c->d_tables + rp->off_lo;
+        a.hi_e = c->d_tables + rp->off_hi;
+        a.partial = c->d_partial;
+    }
+    a.lo_size = ref->lo_size;
+    int sh = 0;
+    while ((int64_t(1) << sh) < ref->lo_size) ++sh;
+    a.lo_shift = sh;
+    a.grid = c->max_grid;
+    a.diag_fast = ref->n_in >= 2 && ref->nk > ref->j;
+    QCHECK(c, launch_step(c->M, c->form, a, c->st), "step kernel");
+    if (rp) QCHECK(c, launch_rho_reduce(c->d_partial, a.grid, c->M2, rho_slot, c->st), "rho reduce kernel");
+    return QUAPI_OK;
+}
+
+quapi_status run_grow_op(quapi_ctx* c, const OpPlan& gp, const void* A_in, void* A_out) {
+    int sh = 0;
+    while ((int64_t(1) << sh) < gp.lo_size) ++sh;
+    QCHECK(c, launch_grow(c->M, c->form, A_in, A_out, ipow(c->M2, gp.n_in), c->d_tables + gp.off_lo,
+                          c->d_tables + gp.off_hi, gp.lo_size, sh, c->st),
+           "grow kernel");
+    return QUAPI_OK;
+}
+
+// The operation that adds path point n to A_in (n_in = min(n, L) digits).
+quapi_status run_point(quapi_ctx* c, int64_t n, const void* A_in, void* A_out, double2* rho_slot) {
+    const OpPlan* rp = nullptr;
+    if (rho_slot) rp = (n <= c->L) ? &c->read_ops[n] : &c->read_steady;
+    if (n < c->L) {
+        if (rp) {
+            quapi_status s = run_step_op(c, nullptr, rp, A_in, nullptr, rho_slot);
+            if (s != QUAPI_OK) return s;
+        }
+        if (A_out) return run_grow_op(c, c->grow_ops[n], A_in, A_out);
+        return QUAPI_OK;
+    }
+    const OpPlan* sp = (n == c->L) ? &c->step_first : &c->step_steady;
+    if (!A_out) sp = nullptr;
+    if (!sp && !rp) return QUAPI_OK;
+    return run_step_op(c, sp, rp, A_in, A_out, rho_slot);
+}
+
+quapi_status check_steps(quapi_ctx* c, const int64_t* steps, int nsteps) {
+    if (!steps || nsteps < 1) return fail(c, QUAPI_ERR_ARG, "steps must hold at least one entry");
+    for (int i = 0; i < nsteps; ++i) {
+        if (steps[i] < 0) return fail(c, QUAPI_ERR_ARG, "steps must be >= 0");
+        if (i > 0 && steps[i] <= steps[i - 1]) return fail(c, QUAPI_ERR_ARG, "steps must be strictly ascending");
+    }
+    return QUAPI_OK;
+}
+
+// Enqueue the whole propagation; rho(t_steps[i]) lands in slots[i] (device).
+quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int64_t* steps, int nsteps,
+                               double2* slots) {
+    const int64_t N = steps[nsteps - 1];
+    int next = 0;
+    if (steps[0] == 0) {
+        QCHECK(c, cudaMemcpyAsync(slots, rho0_dev, sizeof(double2) * c->M2, cudaMemcpyDeviceToDevice, c->st),
+               "copy rho0");
+        next = 1;
+    }
+    if (N == 0) return QUAPI_OK;
+    int cur = 0;
+    QCHECK(c, launch_init_tensor(rho0_dev, c->d_eta, eta_self0(c->L), c->d_s, c->M, c->form, c->buf[cur], c->st),
+           "init tensor kernel");
+    for (int64_t n = 1; n <= N; ++n) {
+        double2* slot = nullptr;
+        if (next < nsteps && steps[next] == n) {
+            slot = slots + (size_t)next * c->M2;
+            ++next;
+        }
+        void* A_out = (n < N) ? c->buf[cur ^ 1] : nullptr;
+        quapi_status s = run_point(c, n, c->buf[cur], A_out, slot);
+        if (s != QUAPI_OK) return s;
+        if (A_out) cur ^= 1;
+    }
+    return QUAPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void quapi_opts_init(quapi_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = QUAPI_FP64;
+    o->endpoint_mode = QUAPI_ENDPOINT_STRANG;
+}
+
+quapi_status quapi_query_memory(int M, int dkmax, int precision, size_t* tensor_bytes, size_t* total_bytes) {
+    if (!tensor_bytes && !total_bytes) return fail(nullptr, QUAPI_ERR_ARG, "no output pointer");
+    if (M != 2 && M != 3) return fail(nullptr, QUAPI_ERR_ARG, "M must be 2 or 3");
+    if (dkmax < 1 || dkmax > max_dkmax(M)) return fail(nullptr, QUAPI_ERR_ARG, "dkmax out of range");
+    if (precision != QUAPI_FP64 && precision != QUAPI_FP32)
+        return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64 or QUAPI_FP32");
+    const size_t t = 2 * (size_t)ipow(M * M, dkmax) * elem_bytes(precision);
+    if (tensor_bytes) *tensor_bytes = t;
+    if (total_bytes) {
+        size_t tb = tables_bytes_for(M, dkmax, QUAPI_ENDPOINT_STRANG);
+        *total_bytes = t + tb + (size_t)16 * M * M * 152 * 16 + 4096;
+    }
+    return QUAPI_OK;
+}
+
+quapi_status quapi_setup(const double* s, int M, const double* H, const quapi_spectral* J, double beta, double dt,
+                         int dkmax, const quapi_opts* opts, quapi_ctx** out) {
+    return setup_impl(s, M, H, J, beta, nullptr, dt, dkmax, opts, out);
+}
+
+quapi_status quapi_setup_eta(const double* s, int M, const double* H, const double* eta, double dt, int dkmax,
+                             const quapi_opts* opts, quapi_ctx** out) {
+    if (!eta) return fail(nullptr, QUAPI_ERR_ARG, "eta must not be NULL");
+    for (int i = 0; i < 2 * (4 * dkmax + 3) && dkmax >= 1 && dkmax <= 16; ++i)
+        if (!std::isfinite(eta[i])) return fail(nullptr, QUAPI_ERR_ARG, "eta must be finite");
+    return setup_impl(s, M, H, nullptr, 1.0, eta, dt, dkmax, opts, out);
+}
+
+quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const int64_t* steps, int nsteps,
+                                    void* rho_out_dev) {
+    if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
+    if (!rho0_dev || !rho_out_dev) return fail(c, QUAPI_ERR_ARG, "rho0 and rho_out must not be NULL");
+    quapi_status s = check_steps(c, steps, nsteps);
+    if (s != QUAPI_OK) return s;
+    return propagate_enqueue(c, static_cast<const double2*>(rho0_dev), steps, nsteps,
+                             static_cast<double2*>(rho_out_dev));
+}
+
+quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* steps, int nsteps, double* rho_out) {
+    if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
+    if (!rho0 || !rho_out) return fail(c, QUAPI_ERR_ARG, "rho0 and rho_out must not be NULL");
+    quapi_status s = check_steps(c, steps, nsteps);
+    if (s != QUAPI_OK) return s;
+    if (c->slots_cap < (size_t)nsteps) {
+        if (c->d_slots) cudaFree(c->d_slots);
+        c->d_slots = nullptr;
+        c->slots_cap = 0;
+        QCHECK(c, cudaMalloc(&c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps), "cudaMalloc(rho slots)");
+        c->slots_cap = nsteps;
+    }
+    QCHECK(c, cudaMemcpyAsync(c->d_rho0, rho0, sizeof(double2) * c->M2, cudaMemcpyHostToDevice, c->st), "copy rho0");
+    s = propagate_enqueue(c, c->d_rho0, steps, nsteps, c->d_slots);
+    if (s != QUAPI_OK) return s;
+    QCHECK(c, cudaMemcpyAsync(rho_out, c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                              c->st),
+           "copy rho");
+    QCHECK(c, cudaStreamSynchronize(c->st), "propagate synchronize");
+    return QUAPI_OK;
+}
+
+quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, void* A_out_dev, void* rho_dev) {
+    if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
+    if (n < 1) return fail(c, QUAPI_ERR_ARG, "n must be >= 1");
+    if (!A_in_dev || (!A_out_dev && !rho_dev)) return fail(c, QUAPI_ERR_ARG, "need A_in and an output");
+    return run_point(c, n, A_in_dev, A_out_dev, static_cast<double2*>(rho_dev));
+}
+
+quapi_status quapi_get_eta(const quapi_ctx* c, double* eta_out) {
+    if (!c || !eta_out) return fail(const_cast<quapi_ctx*>(c), QUAPI_ERR_ARG, "NULL argument");
+    quapi_ctx* m = const_cast<quapi_ctx*>(c);
+    QCHECK(m, cudaMemcpyAsync(eta_out, c->d_eta, sizeof(double2) * (4 * c->L + 3), cudaMemcpyDeviceToHost, c->st),
+           "copy eta");
+    QCHECK(m, cudaStreamSynchronize(c->st), "synchronize");
+    return QUAPI_OK;
+}
+
+quapi_status quapi_get_propagator(const quapi_ctx* c, double* U_out, double* K_out) {
+    if (!c || !U_out) return fail(const_cast<quapi_ctx*>(c), QUAPI_ERR_ARG, "NULL argument");
+    quapi_ctx* m = const_cast<quapi_ctx*>(c);
+    QCHECK(m, cudaMemcpyAsync(U_out, c->d_U, sizeof(double2) * c->M * c->M, cudaMemcpyDeviceToHost, c->st), "copy U");
+    if (K_out)
+        QCHECK(m, cudaMemcpyAsync(K_out, c->d_K, sizeof(double2) * c->M2 * c->M2, cudaMemcpyDeviceToHost, c->st),
+               "copy K");
+    QCHECK(m, cudaStreamSynchronize(c->st), "synchronize");
+    return QUAPI_OK;
+}
+
+quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
+                                   const int64_t* nsteps_each, double* const* rho_final) {
+    (void)n;
+    (void)ctxs;
+    (void)rho0s;
+    (void)nsteps_each;
+    (void)rho_final;
+    return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "batched propagation not built yet");
+}
+
+uint64_t quapi_kernel_launches(void) { return launches_so_far(); }
+
+const char* quapi_last_error(const quapi_ctx* c) {
+    if (c) return c->err.c_str();
+    return g_thread_error.c_str();
+}
+
+void quapi_destroy(quapi_ctx* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    cudaFree(c->d_s);
+    cudaFree(c->d_H);
+    cudaFree(c->d_U);
+    cudaFree(c->d_K);
+    cudaFree(c->d_eta);
+    cudaFree(c->d_rho0);
+    cudaFree(c->d_slots);
+    if (c->own_buf) {
+        cudaFree(c->buf[0]);
+        cudaFree(c->buf[1]);
+    }
+    cudaFree(c->d_tables);
+    cudaFree(c->d_partial);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations shared by the translation units of libquapi.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "quapi.h"
+
+namespace quapi {
+
+constexpr int kMaxDigits = 16;      // L <= 16 for M = 2 (4^16 entries), L <= 10 for M = 3
+constexpr int kThreads = 256;       // threads per CTA of the step / growth kernels
+
+// ---------------------------------------------------------------------------
+// Complex helpers (FP64 and FP32) and double-float ("hi + lo") table entries.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// Table entry of the FP32 form: the FP64 value v split as hi = RN32(v), lo = RN32(v - hi),
+// stored {hi.re, hi.im, lo.re, lo.im}.
+struct __align__(16) ff2 {
+    float hr, hi, lr, li;
+};
+
+// Exact sum of two floats: s + e == a + b (Knuth's TwoSum, no branch).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (T.hi + T.lo) * v for an FP32 complex v, rounded once at the end; the small
+// terms are accumulated first.
+__device__ __forceinline__ float2 ffmul(const ff2& T, float2 v) {
+    float re = fmaf(T.lr, v.x, -T.li * v.y);
+    float im = fmaf(T.lr, v.y, T.li * v.x);
+    re = fmaf(T.hr, v.x, fmaf(-T.hi, v.y, re));
+    im = fmaf(T.hr, v.y, fmaf(T.hi, v.x, im));
+    return make_float2(re, im);
+}
+
+// (T.hi + T.lo) * (s + c) where (s, c) is a compensated FP32 value (|c| << |s|).
+__device__ __forceinline__ float2 ffmul2(const ff2& T, float2 s, float2 c) {
+    float re = fmaf(T.lr, s.x, -T.li * s.y);
+    float im = fmaf(T.lr, s.y, T.li * s.x);
+    re = fmaf(T.hr, c.x, fmaf(-T.hi, c.y, re));
+    im = fmaf(T.hr, c.y, fmaf(T.hi, c.x, im));
+    re = fmaf(T.hr, s.x, fmaf(-T.hi, s.y, re));
+    im = fmaf(T.hr, s.y, fmaf(T.hi, s.x, im));
+    return make_float2(re, im);
+}
+
+// Compensated complex accumulator (Neumaier-style, via TwoSum on each part).
+struct cacc32 {
+    float2 s, c;
+    __device__ __forceinline__ void init(float2 v) { s = v; c = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(float2 v) {
+        float sx, ex, sy, ey;
+        two_sum(s.x, v.x, sx, ex);
+        two_sum(s.y, v.y, sy, ey);
+        s = make_float2(sx, sy);
+        c.x += ex;
+        c.y += ey;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side description of one tensor operation (growth, step or readout).
+// ---------------------------------------------------------------------------
+enum OpKind { OP_GROW = 0, OP_STEP = 1, OP_READ = 2 };
+
+struct OpPlan {
+    int kind = OP_STEP;
+    int n_in = 0;        // digits of the input tensor
+    int summed = 0;      // 1 if digit 0 is summed (step, readout)
+    int nk = 0;          // kept digits (n_in - summed)
+    int j = 0;           // kept digits resolved by the lo table
+    int64_t lo_size = 1; // (M^2)^j
+    int64_t hi_size = 1; // (M^2)^(nk - j)
+    int eta_idx[kMaxDigits] = {0};  // eta index (into the 4L+3 vector) per input digit
+    int self_idx = 0;    // eta index of the new point's self term
+    size_t off_isum = 0, off_lo = 0, off_hi = 0;  // byte offsets in the table arena
+};
+
+// Device-side build request for one OpPlan (all pointers device).
+struct BuildDesc {
+    int M, M2, n_in, summed, nk, j, form;   // form: 64 or 32
+    int eta_idx[kMaxDigits];
+    int self_idx;
+    int64_t lo_size, hi_size;
+    const double2* eta;
+    const double* s;
+    const double2* K;
+    void* isum;
+    void* lo;
+    void* hi;
+};
+
+// eta quadrature request: one integral per entry.
+struct EtaJob {
+    double w1, w2, D;   // box widths (later, earlier) and centre distance; w2 < 0 marks a self box
+};
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the .cu files.
+// ---------------------------------------------------------------------------
+cudaError_t launch_eta_quadrature(const EtaJob* jobs_dev, int njobs, int kind, double a, double wc,
+                                  double beta, int panels, const double* gl_dev, int gl_n,
+                                  double2* eta_out, cudaStream_t st);
+void gauss_legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w);
+
+cudaError_t launch_propagator(const double2* H_dev, int M, double dt, double2* U_dev, double2* K_dev,
+                              cudaStream_t st);
+cudaError_t launch_build_tables(const BuildDesc* descs_dev, int ndesc, int M2, int64_t max_entries,
+                                cudaStream_t st);
+
+struct StepArgs {
+    const void* A_in;
+    void* A_out;          // may be null (readout only)
+    int64_t F;            // input fibers = (M^2)^(n_in - 1)
+    const void* isum;     // step tables
+    const void* lo;
+    const void* hi;
+    const void* isum_e;   // readout tables (null if no readout)
+    const void* lo_e;
+    const void* hi_e;
+    int64_t lo_size;      // (M^2)^j, common to step and readout tables
+    int lo_shift;         // log2(lo_size) when M = 2
+    double2* partial;     // [grid][M^2] readout partial sums
+    int grid;             // in: upper bound (partial buffer size); out: CTAs launched
+    bool diag_fast;
+};
+
+cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st);  // sets a.grid
+cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t S, const void* lo,
+                        const void* hi, int64_t lo_size, int lo_shift, cudaStream_t st);
+cudaError_t launch_rho_reduce(const double2* partial, int nparts, int M2, double2* rho_out,
+                              cudaStream_t st);
+cudaError_t launch_init_tensor(const double2* rho0_dev, const double2* eta, int self0_idx,
+                               const double* s, int M, int form, void* A_out, cudaStream_t st);
+int num_sms();
+
+// process-wide count of kernel launches issued by this library
+void count_launch(uint64_t n = 1);
+uint64_t launches_so_far();
+
+}  // namespace quapi

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances: FP64 form 1e-12 max abs on rho elements; FP32 form 1e-5 max abs on
+rho.  Single-step checks on random tensors compare every output element,
+relative to the largest input magnitude times the number of factors.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.recurrence as rec
+from oracle.eta import Spectral
+from paper_1205_6872_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def q():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1205_6872_gb300 import quapi
+    quapi.load()
+    return quapi
+
+
+def _problem(M, seed=3):
+    if M == 2:
+        return dict(s=np.array([1.0, -1.0]), H=np.array([[0.5, 1.0], [1.0, -0.5]], complex),
+                    spec=Spectral("ohmic_exp", 0.3, 5.0), beta=1.0, dt=0.1,
+                    rho0=np.array([[1, 0], [0, 0]], complex))
+    return dict(s=np.array([-1.0, 0.0, 1.0]), H=wl.random_hermitian(3, seed),
+                spec=Spectral("superohmic_gauss", 0.05, 2.0), beta=2.0, dt=0.2,
+                rho0=wl.random_pure_state(3, seed + 1))
+
+
+def _ctx(q, pr, L, prec, eta=None, endpoint=0):
+    opts = q.quapi_opts_init(precision=prec, endpoint_mode=endpoint)
+    if eta is not None:
+        return q.quapi_setup_eta(pr["s"], pr["H"], eta, pr["dt"], L, opts)
+    return q.quapi_setup(pr["s"], pr["H"], pr["spec"].kind, pr["spec"].a, pr["spec"].wc, pr["beta"],
+                         pr["dt"], L, opts)
+
+
+# ---------------------------------------------------------------- setup kernels
+
+@pytest.mark.parametrize("M,L", [(2, 1), (2, 6), (2, 14), (3, 4)])
+def test_eta_quadrature_matches_oracle(q, M, L):
+    pr = _problem(M)
+    ctx = _ctx(q, pr, L, q.QUAPI_FP64)
+    try:
+        got = q.quapi_get_eta(ctx, L)
+    finally:
+        q.quapi_destroy(ctx)
+    want = oracle.pack_eta(oracle.eta_table(pr["spec"], pr["beta"], pr["dt"], L))
+    err = np.abs(got - want)
+    assert err.max() <= 1e-14 + 1e-13 * np.abs(want).max(), err.max()
+
+
+@pytest.mark.parametrize("name", ["spin_boson_L6", "biased_L12", "three_level_L8", "spin_boson_L14"])
+def test_eta_workloads(q, name):
+    p = wl.CONFIGS[name]()
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init())
+    try:
+        got = q.quapi_get_eta(ctx, p.L)
+    finally:
+        q.quapi_destroy(ctx)
+    want = oracle.pack_eta(oracle.eta_table(Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L))
+    assert np.abs(got - want).max() <= 1e-14 + 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_propagator_matches_oracle(q, M):
+    pr = _problem(M)
+    ctx = _ctx(q, pr, 2, q.QUAPI_FP64)
+    try:
+        U, K = q.quapi_get_propagator(ctx, M)
+    finally:
+        q.quapi_destroy(ctx)
+    Uo = oracle.propagator_U(pr["H"], pr["dt"])
+    assert np.abs(U - Uo).max() < 1e-14
+    assert np.abs(K - oracle.pair_propagator_K(Uo)).max() < 1e-14
+
+
+# ---------------------------------------------------------------- single steps on random tensors
+
+def _to_dev(a, prec):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    t = t.to(torch.complex128 if prec == 64 else torch.complex64)
+    return t.cuda()
+
+
+STEP_CASES = [
+    # (M, L, n): growth steps (n < L), the first summing step (n == L), steady steps
+    (2, 6, 1), (2, 6, 3), (2, 6, 5), (2, 6, 6), (2, 6, 7), (2, 6, 40),
+    (2, 1, 1), (2, 1, 9), (2, 2, 2), (2, 5, 12), (2, 9, 9), (2, 9, 30),
+    (3, 4, 2), (3, 4, 4), (3, 4, 11), (3, 1, 3), (3, 6, 6), (3, 6, 8),
+]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("M,L,n", STEP_CASES)
+def test_single_step_random_tensor(q, M, L, n, prec):
+    pr = _problem(M)
+    eta = wl.random_eta(L, seed=100 + L + n)
+    etad = oracle.unpack_eta(eta, L)
+    K = oracle.pair_propagator_K(oracle.propagator_U(pr["H"], pr["dt"]))
+    M2 = M * M
+    n_in = min(n, L)
+    A = wl.random_tensor(M2 ** n_in, seed=7 * n + L)
+    if prec == 32:
+        A = A.astype(np.complex64).astype(np.complex128)  # both sides see the same FP32 input
+    G, g, n_in_o, summed = rec.step_tables(etad, pr["s"], K, L, n)
+    want = rec.apply_step(A, G, g, n_in_o, summed)
+    Gr, gr, _ = rec.readout_tables(etad, pr["s"], K, L, n)
+    want_rho = rec.apply_readout(A, Gr, gr, n_in_o)
+    ctx = _ctx(q, pr, L, prec, eta=eta)
+    try:
+        dA = _to_dev(A, prec)
+        dout = torch.empty(want.size, dtype=dA.dtype, device="cuda")
+        drho = torch.zeros(M2, dtype=torch.complex128, device="cuda")
+        q.quapi_step_device(ctx, n, dA, dout, drho)
+        torch.cuda.synchronize()
+        got = dout.cpu().numpy().astype(np.complex128)
+        got_rho = drho.cpu().numpy()
+    finally:
+        q.quapi_destroy(ctx)
+    # element scale: |T| * sum |A| over the summed index
+    scale = np.abs(want).max() + 1.0
+    tol = 1e-13 if prec == 64 else 2e-6
+    assert np.abs(got - want).max() <= tol * scale, np.abs(got - want).max()
+    rscale = np.abs(A).sum() * np.abs(G).max() ** n_in
+    rtol = 1e-13 if prec == 64 else 1e-6
+    assert np.abs(got_rho - want_rho).max() <= rtol * max(1.0, np.abs(want_rho).max()) + 1e-15 * rscale
+
+
+# ---------------------------------------------------------------- full propagations
+
+@pytest.mark.parametrize("endpoint", [0, 1])
+def test_spin_boson_L6_fp64_all_steps(q, endpoint):
+    p = wl.spin_boson_L6()
+    spec = Spectral(p.jkind, p.ja, p.wc)
+    steps = list(range(p.N + 1))
+    want = oracle.propagate(p.s, p.H, spec, p.beta, p.dt, p.L, p.rho0, steps,
+                            endpoint="strang" if endpoint == 0 else "interior")
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                        q.quapi_opts_init(precision=64, endpoint_mode=endpoint))
+    try:
+        got = q.quapi_propagate(ctx, p.rho0, steps, p.M)
+    finally:
+        q.quapi_destroy(ctx)
+    err = max(np.abs(got[i] - want[k]).max() for i, k in enumerate(steps))
+    assert err <= 1e-12, err
+
+
+def test_spin_boson_L6_fp32_all_steps(q):
+    p = wl.spin_boson_L6()
+    spec = Spectral(p.jkind, p.ja, p.wc)
+    steps = list(range(p.N + 1))
+    want = oracle.propagate(p.s, p.H, spec, p.beta, p.dt, p.L, p.rho0, steps)
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(precision=32))
+    try:
+        got = q.quapi_propagate(ctx, p.rho0, steps, p.M)
+    finally:
+        q.quapi_destroy(ctx)
+    err = max(np.abs(got[i] - want[k]).max() for i, k in enumerate(steps))
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
+@pytest.mark.parametrize("M,L,N", [(2, 1, 30), (2, 3, 2), (2, 8, 60), (3, 3, 25), (3, 5, 12)])
+def test_small_propagations(q, M, L, N, prec, tol):
+    pr = _problem(M, seed=5)
+    steps = sorted(set([0, 1, 2, min(L, N), N // 2, N]))
+    want = oracle.propagate(pr["s"], pr["H"], pr["spec"], pr["beta"], pr["dt"], L, pr["rho0"], steps)
+    ctx = _ctx(q, pr, L, prec)
+    try:
+        got = q.quapi_propagate(ctx, pr["rho0"], steps, M)
+    finally:
+        q.quapi_destroy(ctx)
+    for i, k in enumerate(steps):
+        assert np.abs(got[i] - want[k]).max() <= tol, (k, got[i], want[k])
+
+
+def test_only_step_zero(q):
+    pr = _problem(2)
+    ctx = _ctx(q, pr, 4, 64)
+    try:
+        got = q.quapi_propagate(ctx, pr["rho0"], [0], 2)
+    finally:
+        q.quapi_destroy(ctx)
+    assert np.array_equal(got[0], pr["rho0"])
+
+
+# ---------------------------------------------------------------- argument errors
+
+def test_argument_errors(q):
+    pr = _problem(2)
+    with pytest.raises(q.QuapiError) as e:
+        q.quapi_setup(pr["s"], [[0, 1], [2, 0]], "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 4)
+    assert e.value.status == q.QUAPI_ERR_ARG
+    with pytest.raises(q.QuapiError) as e:
+        q.quapi_setup(pr["s"], pr["H"], "ohmic_exp", 0.1, 5.0, 1.0, -0.1, 4)
+    assert e.value.status == q.QUAPI_ERR_ARG
+    with pytest.raises(q.QuapiError) as e:
+        q.quapi_setup(np.zeros(4), np.eye(4), "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 4)
+    assert e.value.status == q.QUAPI_ERR_ARG
+    with pytest.raises(q.QuapiError) as e:
+        q.quapi_setup(pr["s"], pr["H"], "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 0)
+    assert e.value.status == q.QUAPI_ERR_ARG
+    ctx = _ctx(q, pr, 3, 64)
+    try:
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate(ctx, pr["rho0"], [3, 2], 2)
+        assert e.value.status == q.QUAPI_ERR_ARG
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate(ctx, pr["rho0"], [-1, 2], 2)
+        assert e.value.status == q.QUAPI_ERR_ARG
+    finally:
+        q.quapi_destroy(ctx)
