@@ -176,6 +176,28 @@ quapi_status quapi_get_eta(const quapi_ctx* c, double* eta_out);
  * the pair propagator K (M^2 x M^2 complex, K[x'][x]). */
 quapi_status quapi_get_propagator(const quapi_ctx* c, double* U_out, double* K_out);
 
+/* Readout of rho(t_n) out of a caller's A_{n-1}, like quapi_step_device with
+ * A_out_dev = NULL, but without allocating anything.  The paper has no
+ * counterpart: this entry point exists for callers that must not touch the
+ * CUDA allocator at that point, e.g. an application whose memory pool
+ * already holds the free device memory (a raw cudaMalloc would fail), or a
+ * time-critical loop that cannot afford cudaMalloc/cudaFree synchronising
+ * the device.  The readout's per-CTA partial sums go to a fixed array inside
+ * the library (216 KiB per device, kept until the process exits) instead of
+ * the context's buffer.
+ *   c          context from quapi_setup / quapi_setup_eta (its tables are used)
+ *   n          >= 1: the path point whose rho(t_n) is read out
+ *   A_in_dev   A_{n-1}: (M^2)^min(n,L) elements in the context's precision (device)
+ *   rho_dev    M*M complex double (device), receives rho(t_n)
+ * Asynchronous on the context's stream.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose kernels can overlap on the GPU (different streams, or
+ * several host threads) race on it and must be serialised by the caller.
+ * Errors: QUAPI_ERR_ARG (NULL pointers, n < 1, M*M above the 9 partial sums a
+ * slot holds), QUAPI_ERR_CUDA. */
+quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, const void* A_in_dev, void* rho_dev);
+
 /* Number of kernels this library has launched in this process so far (all
  * contexts, all threads).  A diagnostic for benchmarks; never fails. */
 uint64_t quapi_kernel_launches(void);

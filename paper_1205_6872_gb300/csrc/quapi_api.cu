@@ -467,6 +467,37 @@ quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int6
 
 }  // namespace
 
+namespace quapi {
+
+// Launch arguments of the readout of rho(t_n) out of A_{n-1} = A_in, for entry
+// points that supply their own partial-sum buffer (readout_static.cu).
+quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in, StepArgs* a, int* M,
+                                 int* form, cudaStream_t* st) {
+    const OpPlan* rp = (n <= c->L) ? &c->read_ops[n] : &c->read_steady;
+    std::memset(a, 0, sizeof(*a));
+    a->A_in = A_in;
+    a->A_out = nullptr;
+    a->F = ipow(c->M2, rp->n_in - 1);
+    a->isum_e = c->d_tables + rp->off_isum;
+    a->lo_e = c->d_tables + rp->off_lo;
+    a->hi_e = c->d_tables + rp->off_hi;
+    a->lo_size = rp->lo_size;
+    int sh = 0;
+    while ((int64_t(1) << sh) < rp->lo_size) ++sh;
+    a->lo_shift = sh;
+    a->diag_fast = rp->n_in >= 2 && rp->nk > rp->j;
+    *M = c->M;
+    *form = c->form;
+    *st = c->st;
+    return QUAPI_OK;
+}
+
+quapi_status record_error(const quapi_ctx* c, quapi_status st, const char* msg) {
+    return fail(const_cast<quapi_ctx*>(c), st, msg);
+}
+
+}  // namespace quapi
+
 extern "C" {
 
 void quapi_opts_init(quapi_opts* o) {

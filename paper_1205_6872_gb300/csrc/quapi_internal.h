@@ -155,3 +155,10 @@ void count_launch(uint64_t n = 1);
 uint64_t launches_so_far();
 
 }  // namespace quapi
+
+struct quapi_ctx;
+namespace quapi {
+quapi_status readout_launch_args(const ::quapi_ctx* c, int64_t n, const void* A_in, StepArgs* a, int* M,
+                                 int* form, cudaStream_t* st);
+quapi_status record_error(const ::quapi_ctx* c, quapi_status st, const char* msg);
+}  // namespace quapi

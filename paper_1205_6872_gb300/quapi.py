@@ -39,7 +39,7 @@ JKIND = {"ohmic_exp": QUAPI_J_OHMIC_EXP, "superohmic_gauss": QUAPI_J_SUPEROHMIC_
 EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_setup", "quapi_setup_eta",
             "quapi_propagate", "quapi_propagate_device", "quapi_step_device",
             "quapi_propagate_batch", "quapi_get_eta", "quapi_get_propagator",
-            "quapi_kernel_launches", "quapi_last_error", "quapi_destroy")
+            "quapi_readout_static", "quapi_kernel_launches", "quapi_last_error", "quapi_destroy")
 
 
 class quapi_spectral(ctypes.Structure):
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
                                                      ctypes.POINTER(dp), i64p, ctypes.POINTER(dp)]),
             "quapi_get_eta": (ctypes.c_int, [ctxp, dp]),
             "quapi_get_propagator": (ctypes.c_int, [ctxp, dp, dp]),
+            "quapi_readout_static": (ctypes.c_int, [ctxp, ctypes.c_int64, vp, vp]),
             "quapi_kernel_launches": (ctypes.c_uint64, []),
             "quapi_last_error": (ctypes.c_char_p, [ctxp]),
             "quapi_destroy": (None, [ctxp]),
@@ -225,6 +226,11 @@ def quapi_get_propagator(ctx, M):
     K = np.empty(M ** 4, dtype=np.complex128)
     _check(load().quapi_get_propagator(ctx, _dp(U.view(np.float64)), _dp(K.view(np.float64))), ctx)
     return U.reshape(M, M), K.reshape(M * M, M * M)
+
+
+def quapi_readout_static(ctx, n, A_in_dev, rho_dev):
+    """rho(t_n) from A_{n-1} into rho_dev, with the readout scratch in the library's fixed array."""
+    _check(load().quapi_readout_static(ctx, int(n), _dev_ptr(A_in_dev), _dev_ptr(rho_dev)), ctx)
 
 
 def quapi_kernel_launches() -> int:
