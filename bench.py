@@ -189,6 +189,7 @@ def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None
         gen = torch.Generator(device="cuda").manual_seed(1)
         A = torch.randn(n_el, dtype=dt_, device="cuda", generator=gen)
         B = torch.empty_like(A)
+        torch.cuda.synchronize()  # A was filled on torch's current stream
         reps = 20
         with torch.cuda.stream(stream):
             for _ in range(3):
@@ -268,6 +269,48 @@ def run_reference(args):
     return 0
 
 
+def run_kernel_only(args):
+    """The fused steady-state step alone on the spin-boson workload at memory length --dkmax.
+
+    One device buffer (the context's workspace) holds both tensors; 3 warm-up
+    launches, then --reps timed launches.  Used for ncu captures on a small case.
+    """
+    import torch
+    from paper_1205_6872_gb300 import quapi as q
+    from paper_1205_6872_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    p = wl.spin_boson_L14()
+    L = args.dkmax
+    prec = q.QUAPI_FP32 if args.form == "fp32" else q.QUAPI_FP64
+    tbytes, _ = q.quapi_query_memory(p.M, L, prec)
+    ws = torch.empty(tbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, L,
+                        q.quapi_opts_init(precision=prec, cuda_stream=stream, workspace=ws,
+                                          workspace_bytes=tbytes))
+    try:
+        half = tbytes // 2
+        A, B = ws.data_ptr(), ws.data_ptr() + half
+        with torch.cuda.stream(stream):
+            ws.view(torch.float32).normal_()
+        for _ in range(3):
+            q.quapi_step_device(ctx, L + 1, A, B, None)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(args.reps):
+            src, dst = (A, B) if r % 2 == 0 else (B, A)
+            q.quapi_step_device(ctx, L + 1, src, dst, None)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+    finally:
+        q.quapi_destroy(ctx)
+    gbs = tbytes / (ms / 1000.0) / 1e9
+    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, kernel_ms=ms, GBps=gbs)))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,9 +319,16 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the fused steady-state step kernel (profiling case)")
+    ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64"], help="form for --kernel-only")
+    ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_only:
+        return run_kernel_only(args)
 
     import torch
     world, rank, local = dist_setup()
