@@ -149,3 +149,34 @@ class OracleRun:
 def propagate(s, H, spec, beta, dt, L, rho0, steps, eta=None, endpoint="strang"):
     """Convenience wrapper: rho at the requested steps for one problem."""
     return OracleRun(s, H, spec, beta, dt, L, eta=eta, endpoint=endpoint).run(rho0, steps)
+
+
+def step_elements(A, G, g, n_in: int, summed: bool, indices):
+    """Selected output entries of one step, each evaluated on its own (plain Python loops).
+
+    For output index o = x_new * S + i (S = M2^(n_in - summed)), the entry is
+    g[x_new] * prod over the kept digits of G[p][x_new][digit] times either
+    A[i] (growth) or sum_{d0} G[0][x_new][d0] * A[i * M2 + d0] (summed step).
+    """
+    M2 = G.shape[1]
+    kept = n_in - (1 if summed else 0)
+    S = M2 ** kept
+    out = []
+    for o in indices:
+        o = int(o)
+        xn, i = divmod(o, S)
+        prod = complex(g[xn])
+        rest = i
+        for q in range(kept):
+            digit = rest % M2
+            rest //= M2
+            p = q + (1 if summed else 0)
+            prod *= complex(G[p, xn, digit])
+        if summed:
+            acc = 0j
+            for d0 in range(M2):
+                acc += complex(G[0, xn, d0]) * complex(A[i * M2 + d0])
+            out.append(prod * acc)
+        else:
+            out.append(prod * complex(A[i]))
+    return np.array(out, dtype=np.complex128)

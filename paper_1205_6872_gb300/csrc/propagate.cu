@@ -18,6 +18,9 @@
 // 2 outputs per row form one 16-byte store); a warp reads one contiguous span
 // of A_in and writes M2 contiguous 512-byte runs of A_out.  Persistent grid
 // (a multiple of the SM count), static tile order, streaming cache hints.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdio>
 
 #include "quapi_internal.h"
@@ -139,8 +142,8 @@ __device__ __forceinline__ double2 row_sum(const double2* __restrict__ isum_row,
     return s;
 }
 template <int M2>
-__device__ __forceinline__ cacc32 row_sum(const ff2* __restrict__ isum_row, const float2 (&a)[M2]) {
-    cacc32 acc;
+__device__ __forceinline__ kahan32 row_sum(const ff2* __restrict__ isum_row, const float2 (&a)[M2]) {
+    kahan32 acc;
     acc.init(ffmul(isum_row[0], a[0]));
 #pragma unroll
     for (int q = 1; q < M2; ++q) acc.add(ffmul(isum_row[q], a[q]));
@@ -152,8 +155,8 @@ template <int M2> __device__ __forceinline__ double2 plain_sum(const double2 (&a
     for (int q = 1; q < M2; ++q) s = cadd(s, a[q]);
     return s;
 }
-template <int M2> __device__ __forceinline__ cacc32 plain_sum(const float2 (&a)[M2]) {
-    cacc32 acc;
+template <int M2> __device__ __forceinline__ kahan32 plain_sum(const float2 (&a)[M2]) {
+    kahan32 acc;
     acc.init(a[0]);
 #pragma unroll
     for (int q = 1; q < M2; ++q) acc.add(a[q]);
@@ -164,51 +167,157 @@ template <int M2> __device__ __forceinline__ cacc32 plain_sum(const float2 (&a)[
 __device__ __forceinline__ double2 apply_p(const double2& hi, const double2& lo, double2 S) {
     return cmul(hi, cmul(lo, S));
 }
-__device__ __forceinline__ float2 apply_p(const ff2& hi, const ff2& lo, const cacc32& S) {
+__device__ __forceinline__ float2 apply_p(const ff2& hi, const ff2& lo, const kahan32& S) {
     return ffmul(hi, ffmul2(lo, S.s, S.c));
 }
 __device__ __forceinline__ double2 apply_hi(const double2& hi, double2 S) { return cmul(hi, S); }
-__device__ __forceinline__ float2 apply_hi(const ff2& hi, const cacc32& S) { return ffmul2(hi, S.s, S.c); }
+__device__ __forceinline__ float2 apply_hi(const ff2& hi, const kahan32& S) { return ffmul2(hi, S.s, S.c); }
 
+// Tables of one launch: summed-digit and lo tables staged in shared memory,
+// hi tables read through L1/L2 (256 consecutive fibers share one hi entry).
+template <int M, int FORM> struct StepTables {
+    using Tab = typename FormT<FORM>::Tab;
+    static constexpr int M2 = M * M;
+    Tab *isum, *isume, *lo, *loe;
+    const Tab *hi, *hie;
+    uint32_t lo_size;
+    int lo_shift;
+    int64_t hi_size;
+
+    // shared memory of one variant: isum + lo for the step, isume + loe for the readout
+    static __host__ __device__ size_t smem_bytes(int64_t lo_size, bool write, bool read) {
+        return sizeof(Tab) * ((write ? 1 : 0) + (read ? 1 : 0)) * (M2 * M2 + M2 * (size_t)lo_size);
+    }
+    template <bool WRITE, bool READ>
+    __device__ __forceinline__ void stage(const StepArgs& args, unsigned char* smem) {
+        Tab* base = reinterpret_cast<Tab*>(smem);
+        const int64_t one = M2 * M2 + M2 * args.lo_size;
+        isum = base;
+        lo = base + M2 * M2;
+        isume = base + (WRITE ? one : 0);
+        loe = isume + M2 * M2;
+        hi = reinterpret_cast<const Tab*>(args.hi);
+        hie = reinterpret_cast<const Tab*>(args.hi_e);
+        lo_size = (uint32_t)args.lo_size;
+        lo_shift = args.lo_shift;
+        hi_size = args.F / args.lo_size;
+        const Tab* g_isum = reinterpret_cast<const Tab*>(args.isum);
+        const Tab* g_lo = reinterpret_cast<const Tab*>(args.lo);
+        const Tab* g_isume = reinterpret_cast<const Tab*>(args.isum_e);
+        const Tab* g_loe = reinterpret_cast<const Tab*>(args.lo_e);
+        for (int e = threadIdx.x; e < M2 * M2; e += kThreads) {
+            if (WRITE) isum[e] = g_isum[e];
+            if (READ) isume[e] = g_isume[e];
+        }
+        for (int e = threadIdx.x; e < M2 * (int)lo_size; e += kThreads) {
+            if (WRITE) lo[e] = g_lo[e];
+            if (READ) loe[e] = g_loe[e];
+        }
+    }
+};
+
+// All outputs (and readout contributions) of the FPT fibers f0.. held in registers.
+template <int M, int FORM, bool WRITE, bool READ, bool DIAG>
+__device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
+                                               typename FormT<FORM>::Elem (&a)[FormT<FORM>::FPT][M * M],
+                                               const bool (&valid)[FormT<FORM>::FPT], int64_t f0, int64_t F,
+                                               typename FormT<FORM>::Elem* __restrict__ out,
+                                               RhoAcc<FORM> (&racc)[M * M]) {
+    constexpr int M2 = M * M;
+    using Elem = typename FormT<FORM>::Elem;
+    constexpr int FPT = FormT<FORM>::FPT;
+    uint32_t fhi[FPT], flo[FPT];
+#pragma unroll
+    for (int u = 0; u < FPT; ++u) Split<M>::split((uint32_t)(f0 + u), T.lo_size, T.lo_shift, fhi[u], flo[u]);
+
+    // diagonal rows: shared plain sum, only K (in hi) applies
+    decltype(plain_sum<M2>(a[0])) Sd[FPT];
+    if (DIAG) {
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) Sd[u] = plain_sum<M2>(a[u]);
+    }
+    // the FPT fibers of a thread share their hi entry when lo_size >= FPT and f0 is a multiple of FPT
+    const bool shared_hi = (FPT == 1) || (T.lo_size >= (uint32_t)FPT && fhi[0] == fhi[FPT - 1]);
+#pragma unroll
+    for (int x = 0; x < M2; ++x) {
+        Elem vout[FPT];
+        Elem vread[FPT];
+        const bool diag_row = DIAG && is_diag<M>(x);
+        typename FormT<FORM>::Tab h0, he0;
+        if (WRITE) h0 = T.hi[(int64_t)x * T.hi_size + fhi[0]];
+        if (READ && !(WRITE && diag_row)) he0 = T.hie[(int64_t)x * T.hi_size + fhi[0]];
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) {
+            if (!valid[u]) {
+                vout[u] = Elem{};
+                vread[u] = Elem{};
+                continue;
+            }
+            const bool same = (u == 0) || shared_hi;
+            if (diag_row) {
+                const int64_t hidx = (int64_t)x * T.hi_size + fhi[u];
+                if (WRITE) {
+                    vout[u] = apply_hi(same ? h0 : T.hi[hidx], Sd[u]);
+                    vread[u] = vout[u];
+                } else {
+                    vread[u] = apply_hi(same ? he0 : T.hie[hidx], Sd[u]);
+                }
+            } else {
+                if (WRITE) {
+                    auto S = row_sum<M2>(T.isum + x * M2, a[u]);
+                    vout[u] = apply_p(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]], T.lo[x * T.lo_size + flo[u]], S);
+                }
+                if (READ) {
+                    auto Se = row_sum<M2>(T.isume + x * M2, a[u]);
+                    vread[u] = apply_p(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]],
+                                       T.loe[x * T.lo_size + flo[u]], Se);
+                }
+            }
+            if (READ) racc[x].add(vread[u]);
+        }
+        if (WRITE) store_row<M, FORM>(out, (int64_t)x * F + f0, vout, valid);
+    }
+}
+
+// Per-CTA readout partial sums: warp trees, then warp sums in warp order.
+template <int M2, int FORM>
+__device__ __forceinline__ void write_partials(const RhoAcc<FORM> (&racc)[M2], double2* partial) {
+    __shared__ double2 red[kThreads / 32][M2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int x = 0; x < M2; ++x) {
+        double2 v = racc[x].value();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) red[warp][x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M2) {
+        double2 v = make_double2(0.0, 0.0);
+        for (int w = 0; w < kThreads / 32; ++w) v = cadd(v, red[w][threadIdx.x]);
+        partial[(int64_t)blockIdx.x * M2 + threadIdx.x] = v;
+    }
+}
+
+// Fused step, plain vectorised global loads (any M, any tensor size).
 template <int M, int FORM, bool WRITE, bool READ, bool DIAG>
 __global__ void __launch_bounds__(kThreads) step_kernel(StepArgs args) {
     constexpr int M2 = M * M;
-    using F_ = FormT<FORM>;
-    using Elem = typename F_::Elem;
-    using Tab = typename F_::Tab;
-    constexpr int FPT = F_::FPT;
+    using Elem = typename FormT<FORM>::Elem;
+    constexpr int FPT = FormT<FORM>::FPT;
     constexpr int TILE = kThreads * FPT;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Tab* s_isum = reinterpret_cast<Tab*>(smem_raw);
-    Tab* s_isume = s_isum + M2 * M2;
-    Tab* s_lo = s_isume + M2 * M2;
-    Tab* s_loe = s_lo + M2 * args.lo_size;
-
-    const Tab* g_isum = reinterpret_cast<const Tab*>(args.isum);
-    const Tab* g_lo = reinterpret_cast<const Tab*>(args.lo);
-    const Tab* g_hi = reinterpret_cast<const Tab*>(args.hi);
-    const Tab* g_isume = reinterpret_cast<const Tab*>(args.isum_e);
-    const Tab* g_loe = reinterpret_cast<const Tab*>(args.lo_e);
-    const Tab* g_hie = reinterpret_cast<const Tab*>(args.hi_e);
-    const uint32_t lo_size = (uint32_t)args.lo_size;
-    const int64_t hi_size = args.F / args.lo_size;
-
-    for (int e = threadIdx.x; e < M2 * M2; e += kThreads) {
-        if (WRITE) s_isum[e] = g_isum[e];
-        if (READ) s_isume[e] = g_isume[e];
-    }
-    for (int e = threadIdx.x; e < M2 * (int)lo_size; e += kThreads) {
-        if (WRITE) s_lo[e] = g_lo[e];
-        if (READ) s_loe[e] = g_loe[e];
-    }
+    StepTables<M, FORM> T;
+    T.template stage<WRITE, READ>(args, smem_raw);
     __syncthreads();
 
     RhoAcc<FORM> racc[M2];
-    if (READ) {
 #pragma unroll
-        for (int x = 0; x < M2; ++x) racc[x].init();
-    }
+    for (int x = 0; x < M2; ++x) racc[x].init();
 
     const Elem* __restrict__ A = reinterpret_cast<const Elem*>(args.A_in);
     Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
@@ -221,73 +330,161 @@ __global__ void __launch_bounds__(kThreads) step_kernel(StepArgs args) {
         bool valid[FPT];
         load_fibers<M2, FORM>(A, f0, F, a, valid);
         if (!valid[0]) continue;
+        process_fibers<M, FORM, WRITE, READ, DIAG>(T, a, valid, f0, F, out, racc);
+    }
+    if (READ) write_partials<M2, FORM>(racc, args.partial);
+}
 
-        uint32_t fhi[FPT], flo[FPT];
-#pragma unroll
-        for (int u = 0; u < FPT; ++u) Split<M>::split((uint32_t)(f0 + u), lo_size, args.lo_shift, fhi[u], flo[u]);
+// ---- TMA-staged variant (M = 2) -------------------------------------------------
+//
+// The input tensor is viewed as rows of 128 bytes (4 FP32 fibers or 2 FP64
+// fibers per row).  Each tile is one 2-D TMA box of 128 rows (16 KB) loaded
+// with the 128-byte swizzle: the 16-byte chunk c of row r lands at chunk
+// position c ^ (r mod 8), so that the 8 threads of a quarter warp, each reading
+// one 16-byte chunk of its own 64-byte slice, hit 8 different bank groups.
+// A ring of STAGES tiles per CTA (one mbarrier each) keeps STAGES x 16 KB of
+// loads in flight while the CTA computes and stores; one thread issues the
+// copies.  Every wait is bounded (globaltimer); on expiry the CTA records the
+// error flag, drains its own copies (bounded) and exits.
+constexpr int kTmaRows = 128;
+constexpr int kTmaTileBytes = kTmaRows * 128;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kBarBytes = 64;                     // mbarrier slot ahead of the tables
 
-        // diagonal rows: shared plain sum, only K (in hi) applies
-        decltype(plain_sum<M2>(a[0])) Sd[FPT];
-        if (DIAG) {
-#pragma unroll
-            for (int u = 0; u < FPT; ++u) Sd[u] = plain_sum<M2>(a[u]);
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap* map, int32_t row, uint32_t bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(bar), "l"(policy)
+        : "memory");
+}
+
+template <int M, int FORM, bool WRITE, bool READ, bool DIAG, int STAGES>
+__global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constant__ CUtensorMap in_map,
+                                                            StepArgs args) {
+    static_assert(M == 2, "the TMA path covers M = 2 (fibers pack whole 128-byte rows)");
+    constexpr int M2 = M * M;
+    using Elem = typename FormT<FORM>::Elem;
+    constexpr int FPT = FormT<FORM>::FPT;
+    constexpr int TILE = kThreads * FPT;  // fibers per 16 KB tile
+    static_assert(TILE * M2 * (int)sizeof(Elem) == kTmaTileBytes, "tile = one TMA box");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    static_assert(STAGES * 8 <= kBarBytes, "mbarriers fit their slot");
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + STAGES * kTmaTileBytes);
+    unsigned char* tables = ring + STAGES * kTmaTileBytes + kBarBytes;  // 16-byte aligned
+
+    StepTables<M, FORM> T;
+    T.template stage<WRITE, READ>(args, tables);
+
+    const int64_t F = args.F;
+    const int64_t ntiles = F / TILE;
+    const int64_t my_tiles = (blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    uint64_t policy = 0;
+    if (threadIdx.x == 0) {
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+        for (int st = 0; st < STAGES; ++st) mbar_init(smem_u32(&bars[st]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES && st < my_tiles; ++st) {
+            const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
+            mbar_expect_tx(smem_u32(&bars[st]), kTmaTileBytes);
+            tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows),
+                          smem_u32(&bars[st]), policy);
         }
+    }
+
+    RhoAcc<FORM> racc[M2];
 #pragma unroll
-        for (int x = 0; x < M2; ++x) {
-            Elem vout[FPT];
-            Elem vread[FPT];
-            const bool diag_row = DIAG && is_diag<M>(x);
+    for (int x = 0; x < M2; ++x) racc[x].init();
+    Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
+
+    const int r = threadIdx.x >> 1;            // row of this thread's 64-byte slice
+    const int c0 = (threadIdx.x & 1) << 2;     // first of its four 16-byte chunks
+    for (int64_t k = 0; k < my_tiles; ++k) {
+        const int st = (int)(k % STAGES);
+        const uint32_t parity = (uint32_t)((k / STAGES) & 1);
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[st]), parity, kWaitLimitNs);
+        Elem a[FPT][M2];
+        if (ok) {
+            const unsigned char* row = ring + st * kTmaTileBytes + r * 128;
 #pragma unroll
-            for (int u = 0; u < FPT; ++u) {
-                if (!valid[u]) {
-                    vout[u] = Elem{};
-                    vread[u] = Elem{};
-                    continue;
-                }
-                if (diag_row) {
-                    const int64_t hidx = (int64_t)x * hi_size + fhi[u];
-                    if (WRITE) {
-                        vout[u] = apply_hi(g_hi[hidx], Sd[u]);
-                        vread[u] = vout[u];
-                    } else {
-                        vread[u] = apply_hi(g_hie[hidx], Sd[u]);
-                    }
+            for (int q = 0; q < 4; ++q) {
+                const int pos = (c0 + q) ^ (r & 7);
+                if constexpr (FORM == QUAPI_FP32) {
+                    const float4 v = *reinterpret_cast<const float4*>(row + pos * 16);
+                    const int e0 = 2 * q, e1 = 2 * q + 1;  // entries of the 2-fiber slice
+                    a[e0 / M2][e0 % M2] = make_float2(v.x, v.y);
+                    a[e1 / M2][e1 % M2] = make_float2(v.z, v.w);
                 } else {
-                    if (WRITE) {
-                        auto S = row_sum<M2>(s_isum + x * M2, a[u]);
-                        vout[u] = apply_p(g_hi[(int64_t)x * hi_size + fhi[u]], s_lo[x * lo_size + flo[u]], S);
-                    }
-                    if (READ) {
-                        auto Se = row_sum<M2>(s_isume + x * M2, a[u]);
-                        vread[u] = apply_p(g_hie[(int64_t)x * hi_size + fhi[u]], s_loe[x * lo_size + flo[u]], Se);
-                    }
+                    a[0][q] = *reinterpret_cast<const double2*>(row + pos * 16);
                 }
-                if (READ) racc[x].add(vread[u]);
             }
-            if (WRITE) store_row<M, FORM>(out, (int64_t)x * F + f0, vout, valid);
         }
-    }
-
-    if (READ) {
-        __shared__ double2 red[kThreads / 32][M2];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int x = 0; x < M2; ++x) {
-            double2 v = racc[x].value();
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                v.x += __shfl_down_sync(0xffffffffu, v.x, off);
-                v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+        if (__syncthreads_or(!ok)) {
+            // a copy never completed: record it, wait (bounded) for this CTA's
+            // copies still in flight, and leave
+            if (threadIdx.x == 0) {
+                atomicExch(args.err_flag, 1);
+                for (int64_t j = k; j < my_tiles && j < k + STAGES; ++j)
+                    mbar_wait_bounded(smem_u32(&bars[j % STAGES]), (uint32_t)((j / STAGES) & 1), kWaitLimitNs / 4);
             }
-            if (lane == 0) red[warp][x] = v;
+            return;
         }
-        __syncthreads();
-        if (threadIdx.x < M2) {
-            double2 v = make_double2(0.0, 0.0);
-            for (int w = 0; w < kThreads / 32; ++w) v = cadd(v, red[w][threadIdx.x]);
-            args.partial[(int64_t)blockIdx.x * M2 + threadIdx.x] = v;
+        // stage st is free again: refill it with tile k + STAGES
+        if (threadIdx.x == 0 && k + STAGES < my_tiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of the stage before the copy
+            const int64_t tile = blockIdx.x + (k + STAGES) * gridDim.x;
+            mbar_expect_tx(smem_u32(&bars[st]), kTmaTileBytes);
+            tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows),
+                          smem_u32(&bars[st]), policy);
         }
+        const int64_t f0 = (blockIdx.x + k * gridDim.x) * TILE + (int64_t)threadIdx.x * FPT;
+        bool valid[FPT];
+#pragma unroll
+        for (int u = 0; u < FPT; ++u) valid[u] = true;
+        process_fibers<M, FORM, WRITE, READ, DIAG>(T, a, valid, f0, F, out, racc);
     }
+    if (READ) write_partials<M2, FORM>(racc, args.partial);
 }
 
 template <int M, int FORM>
@@ -327,10 +524,8 @@ __global__ void rho_reduce_kernel(const double2* __restrict__ partial, int npart
 
 template <int M, int FORM, bool W, bool R, bool D>
 cudaError_t launch_variant(StepArgs& a, cudaStream_t st) {
-    using Tab = typename FormT<FORM>::Tab;
-    constexpr int M2 = M * M;
     constexpr int FPT = FormT<FORM>::FPT;
-    size_t smem = sizeof(Tab) * (2 * M2 * M2 + 2 * M2 * (size_t)a.lo_size);
+    size_t smem = StepTables<M, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = step_kernel<M, FORM, W, R, D>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -352,9 +547,83 @@ cudaError_t launch_variant(StepArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D view of a tensor as rows of 32 four-byte words (128 B), 128-row boxes, 128-byte swizzle.
+bool encode_rows_map(CUtensorMap* map, const void* base, int64_t bytes) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || bytes % (128 * kTmaRows) != 0) return false;
+    const int64_t rows = bytes / 128;
+    if (rows > (int64_t(1) << 32)) return false;
+    cuuint64_t dims[2] = {32, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {32, (cuuint32_t)kTmaRows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int FORM, bool W, bool R, bool D, int STAGES>
+cudaError_t launch_tma_variant(StepArgs& a, const CUtensorMap& map, cudaStream_t st) {
+    size_t smem = 1024 + (size_t)STAGES * kTmaTileBytes + kBarBytes + StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+    auto kern = step_kernel_tma<2, FORM, W, R, D, STAGES>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    constexpr int FPT = FormT<FORM>::FPT;
+    const int64_t ntiles = a.F / ((int64_t)kThreads * FPT);
+    int64_t g = (int64_t)num_sms() * occ;
+    if (g > ntiles) g = ntiles;
+    if (g > a.grid) g = a.grid;
+    if (g < 1) g = 1;
+    a.grid = (int)g;
+    kern<<<a.grid, kThreads, smem, st>>>(map, a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <int FORM, bool W, bool R, bool D>
+cudaError_t launch_tma_stages(StepArgs& a, const CUtensorMap& map, cudaStream_t st) {
+    switch (a.stages) {
+        case 2: return launch_tma_variant<FORM, W, R, D, 2>(a, map, st);
+        case 3: return launch_tma_variant<FORM, W, R, D, 3>(a, map, st);
+        case 6: return launch_tma_variant<FORM, W, R, D, 6>(a, map, st);
+        default: return launch_tma_variant<FORM, W, R, D, 4>(a, map, st);
+    }
+}
+
 template <int M, int FORM>
 cudaError_t launch_step_mf(StepArgs& a, cudaStream_t st) {
     const bool W = a.A_out != nullptr, R = a.partial != nullptr;
+    if constexpr (M == 2) if (a.use_tma && a.diag_fast) {
+        constexpr int FPT = FormT<FORM>::FPT;
+        const int64_t elt = (FORM == QUAPI_FP64) ? 16 : 8;
+        CUtensorMap map;
+        if (a.F % ((int64_t)kThreads * FPT) == 0 && encode_rows_map(&map, a.A_in, a.F * M * M * elt)) {
+            if (W && R) return launch_tma_stages<FORM, true, true, true>(a, map, st);
+            if (W) return launch_tma_stages<FORM, true, false, true>(a, map, st);
+            if (R) return launch_tma_stages<FORM, false, true, true>(a, map, st);
+        }
+    }
     if (a.diag_fast) {
         if (W && R) return launch_variant<M, FORM, true, true, true>(a, st);
         if (W) return launch_variant<M, FORM, true, false, true>(a, st);

@@ -69,7 +69,10 @@ struct quapi_ctx {
     bool own_buf = true;
     unsigned char* d_tables = nullptr;
     double2* d_partial = nullptr;
+    int* d_err = nullptr;        // set by a kernel whose bounded wait expired
     int max_grid = 0;
+    bool use_tma = true;         // M = 2: TMA-staged step kernel when the tensor allows it
+    int stages = 2;              // its ring depth (2 measured best: 4 CTAs per SM fit)
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
     OpPlan step_first, step_steady, read_steady;
@@ -286,6 +289,13 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     SCHECK(cudaMalloc(&c->d_tables, cursor + 256), "cudaMalloc(tables)");
     c->max_grid = num_sms() * 8;  // at most 8 resident CTAs of 256 threads per SM
     SCHECK(cudaMalloc(&c->d_partial, sizeof(double2) * M2 * (size_t)c->max_grid), "cudaMalloc(partials)");
+    SCHECK(cudaMalloc(&c->d_err, sizeof(int)), "cudaMalloc(error flag)");
+    SCHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st), "clear error flag");
+    if (const char* v = std::getenv("QUAPI_TMA")) c->use_tma = std::atoi(v) != 0;
+    if (const char* v = std::getenv("QUAPI_STAGES")) {
+        int k = std::atoi(v);
+        if (k == 2 || k == 3 || k == 4 || k == 6) c->stages = k;
+    }
 
     SCHECK(cudaMemcpyAsync(c->d_s, s, sizeof(double) * M, cudaMemcpyHostToDevice, c->st), "copy s");
     SCHECK(cudaMemcpyAsync(c->d_H, H, sizeof(double2) * M * M, cudaMemcpyHostToDevice, c->st), "copy H");
@@ -396,6 +406,9 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
     a.lo_shift = sh;
     a.grid = c->max_grid;
     a.diag_fast = ref->n_in >= 2 && ref->nk > ref->j;
+    a.use_tma = c->use_tma;
+    a.stages = c->stages;
+    a.err_flag = c->d_err;
     QCHECK(c, launch_step(c->M, c->form, a, c->st), "step kernel");
     if (rp) QCHECK(c, launch_rho_reduce(c->d_partial, a.grid, c->M2, rho_slot, c->st), "rho reduce kernel");
     return QUAPI_OK;
@@ -433,6 +446,17 @@ quapi_status check_steps(quapi_ctx* c, const int64_t* steps, int nsteps) {
     for (int i = 0; i < nsteps; ++i) {
         if (steps[i] < 0) return fail(c, QUAPI_ERR_ARG, "steps must be >= 0");
         if (i > 0 && steps[i] <= steps[i - 1]) return fail(c, QUAPI_ERR_ARG, "steps must be strictly ascending");
+    }
+    return QUAPI_OK;
+}
+
+// Reads (and clears) the flag a kernel sets when one of its bounded waits expired.
+quapi_status check_device_error(quapi_ctx* c) {
+    int flag = 0;
+    QCHECK(c, cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read error flag");
+    if (flag) {
+        QCHECK(c, cudaMemset(c->d_err, 0, sizeof(int)), "clear error flag");
+        return fail(c, QUAPI_ERR_TIMEOUT, "a device-side wait gave up (copy never completed)");
     }
     return QUAPI_OK;
 }
@@ -486,6 +510,9 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     while ((int64_t(1) << sh) < rp->lo_size) ++sh;
     a->lo_shift = sh;
     a->diag_fast = rp->n_in >= 2 && rp->nk > rp->j;
+    a->use_tma = c->use_tma;
+    a->stages = c->stages;
+    a->err_flag = c->d_err;
     *M = c->M;
     *form = c->form;
     *st = c->st;
@@ -564,7 +591,7 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
                               c->st),
            "copy rho");
     QCHECK(c, cudaStreamSynchronize(c->st), "propagate synchronize");
-    return QUAPI_OK;
+    return check_device_error(c);
 }
 
 quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, void* A_out_dev, void* rho_dev) {
@@ -628,6 +655,7 @@ void quapi_destroy(quapi_ctx* c) {
     }
     cudaFree(c->d_tables);
     cudaFree(c->d_partial);
+    cudaFree(c->d_err);
     delete c;
 }
 

@@ -60,7 +60,8 @@ __device__ __forceinline__ float2 ffmul2(const ff2& T, float2 s, float2 c) {
     return make_float2(re, im);
 }
 
-// Compensated complex accumulator (Neumaier-style, via TwoSum on each part).
+// Compensated complex accumulator for long sums (TwoSum on each part; the
+// errors are collected in c, value = s + c).
 struct cacc32 {
     float2 s, c;
     __device__ __forceinline__ void init(float2 v) { s = v; c = make_float2(0.f, 0.f); }
@@ -71,6 +72,20 @@ struct cacc32 {
         s = make_float2(sx, sy);
         c.x += ex;
         c.y += ey;
+    }
+};
+
+// Kahan-compensated complex sum for the short sums over the summed path index
+// (4 or 9 terms): value = s + c, with c the negated running correction.
+struct kahan32 {
+    float2 s, c;
+    __device__ __forceinline__ void init(float2 v) { s = v; c = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(float2 v) {
+        float yx = v.x + c.x, yy = v.y + c.y;
+        float tx = s.x + yx, ty = s.y + yy;
+        c.x = yx - (tx - s.x);
+        c.y = yy - (ty - s.y);
+        s = make_float2(tx, ty);
     }
 };
 
@@ -139,6 +154,9 @@ struct StepArgs {
     double2* partial;     // [grid][M^2] readout partial sums
     int grid;             // in: upper bound (partial buffer size); out: CTAs launched
     bool diag_fast;
+    bool use_tma;         // M = 2: stage input tiles with 2-D TMA copies when the tensor allows it
+    int stages;           // TMA ring depth (2, 3, 4 or 6)
+    int* err_flag;        // set to 1 by a CTA whose bounded wait expired
 };
 
 cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st);  // sets a.grid
