@@ -1,0 +1,808 @@
+// Batched propagation: many independent instances (own L, eta, K, N) in one
+// persistent kernel launch, captured once into a CUDA graph and replayed.
+//
+// Work list.  Instances whose two tensors fit in 32 KB of shared memory
+// ("resident") are one work item each: a CTA runs all of that instance's
+// steps in shared memory.  Every other instance contributes, for each step n,
+// ceil(tiles / group) items of `group` tiles (a tile = 256 x FPT fibers or
+// growth entries).  Items are numbered resident first, then step-major
+// (wave n = step n of every instance), so an item only ever depends on items
+// with smaller numbers: a CTA takes the next number from an atomic counter,
+// waits (bounded) until its instance has completed every tile of the previous
+// step, processes its tiles, and publishes the count.  The readout at the
+// instance's final step writes one partial sum per tile; the CTA finishing the
+// last tile adds them in tile order (deterministic result).
+//
+// Launch shape (FPT, group) is chosen per batch signature by timing candidates
+// when tuning is requested (quapi_opts.tune or QUAPI_TUNE=1); the choice is
+// cached in memory and, if QUAPI_TUNE_CACHE names a file, on disk.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "step_math.cuh"
+
+namespace quapi {
+
+namespace {
+
+using namespace math;
+
+constexpr int kBThreads = 256;
+constexpr int kResidentBytes = 32 * 1024;
+
+struct BatchArgs {
+    const BatchInst* inst;
+    const int* resident;        // instance ids run whole in shared memory
+    int nresident;
+    const int* tiled;           // instance ids processed tile by tile
+    int ntiled;
+    int nwaves;                 // largest final step among the tiled instances
+    const int64_t* wave_off;    // [nwaves + 2]: first item of wave n (wave 0 = resident items)
+    const int64_t* inst_off;    // [(nwaves + 1) x (ntiled + 1)]: item offset of tiled instance k in wave n
+    const unsigned* need;       // [(nwaves + 1) x ntiled]: tiles instance k completes before step n
+    const unsigned* ntiles;     // [(nwaves + 1) x ntiled]: tiles of instance k at step n (0: none)
+    int64_t total_items;
+    unsigned long long* next_item;
+    int* err;
+    int group;
+    uint64_t wait_ns;
+};
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int M, int FORM> __device__ __forceinline__ OpTabs<M, FORM> tabs_of(const OpRef& r) {
+    using Tab = typename Form<FORM>::Tab;
+    OpTabs<M, FORM> t;
+    t.isum = reinterpret_cast<const Tab*>(r.isum);
+    t.lo = reinterpret_cast<const Tab*>(r.lo);
+    t.hi = reinterpret_cast<const Tab*>(r.hi);
+    t.lo_size = (uint32_t)r.lo_size;
+    t.lo_shift = r.lo_shift;
+    t.hi_size = r.hi_size;
+    return t;
+}
+
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(v.x, v.y); }
+template <int FORM> __device__ __forceinline__ typename Form<FORM>::Elem from_d(double2 v);
+template <> __device__ __forceinline__ double2 from_d<QUAPI_FP64>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d<QUAPI_FP32>(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+}
+
+__device__ __forceinline__ double2 ld_l2(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
+
+__device__ double2 initial_entry(const BatchInst& I, int M, int x, const double2* rho0) {
+    const double sp = I.s[x / M], sm = I.s[x % M], d = sp - sm;
+    const double2 e = I.eta[I.self0_idx];
+    const double re = -d * (e.x * sp - e.x * sm), im = -d * (e.y * sp + e.y * sm);
+    double sn, cs;
+    sincos(im, &sn, &cs);
+    const double m = exp(re);
+    return cmul(rho0[x], make_double2(m * cs, m * sn));
+}
+
+// Readout accumulator per row: FP64 plain, FP32 TwoSum-compensated.
+template <int FORM> struct Acc;
+template <> struct Acc<QUAPI_FP64> {
+    double2 s;
+    __device__ void init() { s = make_double2(0.0, 0.0); }
+    __device__ void add(double2 v) { s = cadd(s, v); }
+    __device__ double2 value() const { return s; }
+};
+template <> struct Acc<QUAPI_FP32> {
+    cacc32 a;
+    __device__ void init() { a.init(make_float2(0.f, 0.f)); }
+    __device__ void add(float2 v) { a.add(v); }
+    __device__ double2 value() const { return make_double2((double)a.s.x + a.c.x, (double)a.s.y + a.c.y); }
+};
+
+// Block-wide sum of acc (one value per row) in a fixed order; the result is
+// valid in threads 0..M2-1 (thread x holds row x).
+template <int M2, int FORM>
+__device__ double2 block_rows_sum(const Acc<FORM> (&acc)[M2], double2 (*red)[M2]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int x = 0; x < M2; ++x) {
+        double2 v = acc[x].value();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) red[warp][x] = v;
+    }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    if (threadIdx.x < M2)
+        for (int w = 0; w < kBThreads / 32; ++w) r = cadd(r, red[w][threadIdx.x]);
+    __syncthreads();
+    return r;
+}
+
+template <int M, int FORM>
+__device__ void step_fiber_dispatch(const OpRef& op, const typename Form<FORM>::Elem (&a)[M * M], uint32_t f,
+                                    typename Form<FORM>::Elem (&o)[M * M]) {
+    const OpTabs<M, FORM> T = tabs_of<M, FORM>(op);
+    if (op.diag)
+        fiber_step<M, FORM, true>(T, a, f, o);
+    else
+        fiber_step<M, FORM, false>(T, a, f, o);
+}
+
+// One instance, every step in shared memory (resident instances).
+template <int M, int FORM>
+__device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*red)[M * M]) {
+    constexpr int M2 = M * M;
+    using Elem = typename Form<FORM>::Elem;
+    int64_t cap = 1;
+    for (int i = 0; i < I.L; ++i) cap *= M2;
+    Elem* bufA = reinterpret_cast<Elem*>(smem);
+    Elem* bufB = bufA + cap;
+    if (threadIdx.x < M2) bufA[threadIdx.x] = from_d<FORM>(initial_entry(I, M, threadIdx.x, I.rho0));
+    __syncthreads();
+    for (int n = 1; n < I.N; ++n) {
+        if (n < I.L) {
+            const OpTabs<M, FORM> T = tabs_of<M, FORM>(I.grow[n]);
+            int64_t S = 1;
+            for (int i = 0; i < n; ++i) S *= M2;
+            for (int64_t i = threadIdx.x; i < S; i += kBThreads) {
+                Elem o[M2];
+                entry_grow<M, FORM>(T, bufA[i], (uint32_t)i, o);
+#pragma unroll
+                for (int x = 0; x < M2; ++x) bufB[x * S + i] = o[x];
+            }
+        } else {
+            const OpRef& op = (n == I.L) ? I.step_first : I.step;
+            const int64_t F = cap / M2;
+            for (int64_t f = threadIdx.x; f < F; f += kBThreads) {
+                Elem a[M2], o[M2];
+#pragma unroll
+                for (int q = 0; q < M2; ++q) a[q] = bufA[f * M2 + q];
+                step_fiber_dispatch<M, FORM>(op, a, (uint32_t)f, o);
+#pragma unroll
+                for (int x = 0; x < M2; ++x) bufB[x * F + f] = o[x];
+            }
+        }
+        __syncthreads();
+        Elem* t = bufA;
+        bufA = bufB;
+        bufB = t;
+    }
+    // readout of rho(t_N) from A_{N-1}
+    int64_t Fr = 1;
+    for (int i = 1; i < I.read.n_in; ++i) Fr *= M2;
+    Acc<FORM> acc[M2];
+#pragma unroll
+    for (int x = 0; x < M2; ++x) acc[x].init();
+    for (int64_t f = threadIdx.x; f < Fr; f += kBThreads) {
+        Elem a[M2], o[M2];
+#pragma unroll
+        for (int q = 0; q < M2; ++q) a[q] = bufA[f * M2 + q];
+        step_fiber_dispatch<M, FORM>(I.read, a, (uint32_t)f, o);
+#pragma unroll
+        for (int x = 0; x < M2; ++x) acc[x].add(o[x]);
+    }
+    const double2 r = block_rows_sum<M2, FORM>(acc, red);
+    if (threadIdx.x < M2) I.rho_out[threadIdx.x] = r;
+    __syncthreads();
+}
+
+template <int M, int FORM, int FPT>
+__global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs args) {
+    constexpr int M2 = M * M;
+    using Elem = typename Form<FORM>::Elem;
+    constexpr int TE = kBThreads * FPT;  // fibers (or growth entries) per tile
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_stop;
+    __shared__ double2 red[kBThreads / 32][M2];
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int e = *reinterpret_cast<volatile int*>(args.err);
+            s_item = e ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
+        }
+        __syncthreads();
+        const long long g = s_item;
+        __syncthreads();
+        if (g < 0 || g >= args.total_items) break;
+        if (g < args.wave_off[1]) {
+            run_resident<M, FORM>(args.inst[args.resident[g]], smem, red);
+            continue;
+        }
+        // wave (step) n: largest n with wave_off[n] <= g
+        int lo = 1, hi = args.nwaves;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (args.wave_off[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const int n = lo;
+        const int64_t r = g - args.wave_off[n];
+        const int64_t* io = args.inst_off + (int64_t)n * (args.ntiled + 1);
+        int kl = 0, kh = args.ntiled - 1;
+        while (kl < kh) {
+            const int mid = (kl + kh + 1) >> 1;
+            if (io[mid] <= r) kl = mid;
+            else kh = mid - 1;
+        }
+        const int k = kl;
+        const unsigned nt = args.ntiles[(int64_t)n * args.ntiled + k];
+        const unsigned t0 = (unsigned)(r - io[k]) * (unsigned)args.group;
+        const unsigned t1 = min(t0 + (unsigned)args.group, nt);
+        const BatchInst& I = args.inst[args.tiled[k]];
+
+        // every tile of the previous step of this instance must be complete
+        if (threadIdx.x == 0) {
+            const unsigned want = args.need[(int64_t)n * args.ntiled + k];
+            volatile unsigned* d = I.done;
+            int stop = 0;
+            if (*d < want) {
+                const uint64_t t_start = now_ns();
+                while (*d < want) {
+                    if (*reinterpret_cast<volatile int*>(args.err)) {
+                        stop = 1;
+                        break;
+                    }
+                    if (now_ns() - t_start > args.wait_ns) {
+                        atomicExch(args.err, 1);
+                        stop = 1;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+            s_stop = stop;
+        }
+        __syncthreads();
+        if (s_stop) break;
+
+        const void* in = I.buf[(n - 1) & 1];
+        void* outv = I.buf[n & 1];
+        for (unsigned t = t0; t < t1; ++t) {
+            const int64_t base = (int64_t)t * TE + (int64_t)threadIdx.x * FPT;
+            if (n < I.L && n < I.N) {
+                int64_t S = 1;
+                for (int i = 0; i < n; ++i) S *= M2;
+                const OpTabs<M, FORM> T = tabs_of<M, FORM>(I.grow[n]);
+                const Elem* A = reinterpret_cast<const Elem*>(in);
+                Elem* out = reinterpret_cast<Elem*>(outv);
+#pragma unroll
+                for (int u = 0; u < FPT; ++u) {
+                    const int64_t i = base + u;
+                    if (i < S) {
+                        Elem o[M2];
+                        entry_grow<M, FORM>(T, ld_l2(A + i), (uint32_t)i, o);
+#pragma unroll
+                        for (int x = 0; x < M2; ++x) out[x * S + i] = o[x];
+                    }
+                }
+            } else if (n < I.N) {
+                int64_t F = 1;
+                for (int i = 1; i < I.L; ++i) F *= M2;
+                const OpRef& op = (n == I.L) ? I.step_first : I.step;
+                const Elem* A = reinterpret_cast<const Elem*>(in);
+                Elem* out = reinterpret_cast<Elem*>(outv);
+#pragma unroll
+                for (int u = 0; u < FPT; ++u) {
+                    const int64_t f = base + u;
+                    if (f < F) {
+                        Elem a[M2], o[M2];
+#pragma unroll
+                        for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
+                        step_fiber_dispatch<M, FORM>(op, a, (uint32_t)f, o);
+#pragma unroll
+                        for (int x = 0; x < M2; ++x) out[x * F + f] = o[x];
+                    }
+                }
+            } else {
+                int64_t F = 1;
+                for (int i = 1; i < I.read.n_in; ++i) F *= M2;
+                const Elem* A = reinterpret_cast<const Elem*>(in);
+                Acc<FORM> acc[M2];
+#pragma unroll
+                for (int x = 0; x < M2; ++x) acc[x].init();
+#pragma unroll
+                for (int u = 0; u < FPT; ++u) {
+                    const int64_t f = base + u;
+                    if (f < F) {
+                        Elem a[M2], o[M2];
+#pragma unroll
+                        for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
+                        step_fiber_dispatch<M, FORM>(I.read, a, (uint32_t)f, o);
+#pragma unroll
+                        for (int x = 0; x < M2; ++x) acc[x].add(o[x]);
+                    }
+                }
+                const double2 v = block_rows_sum<M2, FORM>(acc, red);
+                if (threadIdx.x < M2) I.partial[(int64_t)t * M2 + threadIdx.x] = v;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    const unsigned prev = atomicAdd(I.read_done, 1u);
+                    s_stop = (prev + 1 == nt) ? 2 : 0;
+                    if (s_stop == 2) __threadfence();
+                }
+                __syncthreads();
+                if (s_stop == 2 && threadIdx.x < M2) {
+                    double2 sum = make_double2(0.0, 0.0);
+                    for (unsigned p = 0; p < nt; ++p) sum = cadd(sum, __ldcg(I.partial + (int64_t)p * M2 + threadIdx.x));
+                    I.rho_out[threadIdx.x] = sum;
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(I.done, t1 - t0);
+        }
+    }
+}
+
+template <int M, int FORM>
+__global__ void batch_init_kernel(const BatchInst* inst, const int* tiled, int ntiled) {
+    const int k = blockIdx.x;
+    if (k >= ntiled) return;
+    const BatchInst& I = inst[tiled[k]];
+    const int x = threadIdx.x;
+    if (x < M * M) {
+        using Elem = typename Form<FORM>::Elem;
+        reinterpret_cast<Elem*>(I.buf[0])[x] = from_d<FORM>(initial_entry(I, M, x, I.rho0));
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+struct Plan {
+    int M = 0, form = 0, fpt = 0, group = 0, n = 0;
+    std::vector<uint64_t> uids;
+    std::vector<int64_t> Ns;
+    std::vector<BatchInst> inst;
+    std::vector<int> resident, tiled;
+    int nwaves = 0;
+    int64_t total_items = 0;
+    int grid = 0;
+    size_t smem = 0;
+    DevBuf d_inst, d_res, d_tiled, d_wave, d_ioff, d_need, d_nt, d_next, d_err, d_cnt, d_part, d_rho0, d_rho;
+    double* h_rho0 = nullptr;  // pinned staging
+    double* h_rho = nullptr;
+    BatchArgs args{};
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t cnt_bytes = 0;
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+        if (h_rho0) cudaFreeHost(h_rho0);
+        if (h_rho) cudaFreeHost(h_rho);
+    }
+};
+
+std::mutex g_plans_mutex;
+std::map<std::string, Plan*> g_plans;
+std::map<std::string, std::pair<int, int>> g_tuned;  // signature -> (fpt, group)
+
+std::string plan_key(const std::vector<uint64_t>& uids, const std::vector<int64_t>& Ns, int fpt, int group) {
+    std::ostringstream o;
+    o << fpt << ":" << group;
+    for (size_t i = 0; i < uids.size(); ++i) o << "|" << uids[i] << "," << Ns[i];
+    return o.str();
+}
+
+int64_t ipow64(int64_t b, int e) {
+    int64_t r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+// tiles of instance (L, N) at step n for the given tile size
+unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin) {
+    if (n < 1 || n > N) return 0;
+    int64_t units;
+    if (n < L && n < N) units = ipow64(M2, n);                  // growth: input entries
+    else if (n < N) units = ipow64(M2, L - 1);                  // step: fibers
+    else units = ipow64(M2, read_nin - 1);                      // readout: fibers
+    return (unsigned)((units + te - 1) / te);
+}
+
+template <int M, int FORM, int FPT> cudaError_t launch_batch(Plan& P, cudaStream_t st, bool prepare_only) {
+    auto kern = batch_kernel<M, FORM, FPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
+    if (e != cudaSuccess) return e;
+    if (P.grid == 0) {
+        int occ = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBThreads, P.smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        P.grid = std::max(1, sms * std::max(occ, 1));
+    }
+    if (prepare_only) return cudaSuccess;
+    if (!P.args.ntiled && !P.args.nresident) return cudaSuccess;
+    if (P.args.ntiled) batch_init_kernel<M, FORM><<<P.args.ntiled, 32, 0, st>>>(P.args.inst, P.args.tiled, P.args.ntiled);
+    kern<<<P.grid, kBThreads, P.smem, st>>>(P.args);
+    return cudaGetLastError();
+}
+
+template <int M, int FORM> cudaError_t launch_batch_fpt(Plan& P, cudaStream_t st, bool prep) {
+    switch (P.fpt) {
+        case 1: return launch_batch<M, FORM, 1>(P, st, prep);
+        case 4: return launch_batch<M, FORM, 4>(P, st, prep);
+        default: return launch_batch<M, FORM, 2>(P, st, prep);
+    }
+}
+
+// prep = true: only set the kernel's shared-memory attribute and size the grid
+cudaError_t launch_plan(Plan& P, cudaStream_t st, bool prep = false) {
+    if (P.M == 2 && P.form == QUAPI_FP32) return launch_batch_fpt<2, QUAPI_FP32>(P, st, prep);
+    if (P.M == 2 && P.form == QUAPI_FP64) return launch_batch_fpt<2, QUAPI_FP64>(P, st, prep);
+    if (P.M == 3 && P.form == QUAPI_FP32) return launch_batch_fpt<3, QUAPI_FP32>(P, st, prep);
+    if (P.M == 3 && P.form == QUAPI_FP64) return launch_batch_fpt<3, QUAPI_FP64>(P, st, prep);
+    return cudaErrorInvalidValue;
+}
+
+template <class T> cudaError_t upload(DevBuf& b, const std::vector<T>& v) {
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&b.p, sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Enqueue one run of the plan: counters cleared, rho0 uploaded, kernels, rho downloaded.
+cudaError_t enqueue_run(Plan& P, cudaStream_t st) {
+    cudaError_t e;
+    const int M2 = P.M * P.M;
+    if ((e = cudaMemsetAsync(P.d_cnt.p, 0, P.cnt_bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(P.d_next.p, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(P.d_rho0.p, P.h_rho0, sizeof(double2) * M2 * P.n, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = launch_plan(P, st)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(P.h_rho, P.d_rho.p, sizeof(double2) * M2 * P.n, cudaMemcpyDeviceToHost, st);
+}
+
+cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int form, int fpt, int group,
+                       uint64_t wait_ns) {
+    cudaError_t e;
+    const int M2 = M * M;
+    const size_t elt = form == QUAPI_FP64 ? 16 : 8;
+    P.M = M;
+    P.form = form;
+    P.fpt = fpt;
+    P.group = group;
+    P.n = (int)insts.size();
+    P.inst = insts;
+    P.smem = kResidentBytes;
+    const int te = kBThreads * fpt;
+    // per-instance buffers
+    if ((e = cudaMalloc(&P.d_rho0.p, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&P.d_rho.p, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&P.h_rho0, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost(&P.h_rho, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
+    std::vector<int64_t> read_tiles(P.n, 0);
+    int64_t part_total = 0;
+    for (int i = 0; i < P.n; ++i) {
+        BatchInst& I = P.inst[i];
+        const bool res = 2 * (size_t)ipow64(M2, I.L) * elt <= (size_t)kResidentBytes;
+        if (res) {
+            P.resident.push_back(i);
+        } else {
+            P.tiled.push_back(i);
+            read_tiles[i] = tiles_at(M2, I.L, I.N, I.N, te, I.read.n_in);
+            part_total += read_tiles[i];
+        }
+    }
+    // counters (done + read_done per instance) and readout partials
+    P.cnt_bytes = sizeof(unsigned) * 2 * std::max(P.n, 1);
+    if ((e = cudaMalloc(&P.d_cnt.p, P.cnt_bytes)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&P.d_part.p, sizeof(double2) * M2 * std::max<int64_t>(part_total, 1))) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&P.d_next.p, sizeof(unsigned long long))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&P.d_err.p, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMemset(P.d_err.p, 0, sizeof(int))) != cudaSuccess) return e;
+    unsigned* cnt = static_cast<unsigned*>(P.d_cnt.p);
+    double2* part = static_cast<double2*>(P.d_part.p);
+    int64_t poff = 0;
+    for (int i = 0; i < P.n; ++i) {
+        BatchInst& I = P.inst[i];
+        I.done = cnt + 2 * i;
+        I.read_done = cnt + 2 * i + 1;
+        I.rho0 = static_cast<double2*>(P.d_rho0.p) + (size_t)M2 * i;
+        I.rho_out = static_cast<double2*>(P.d_rho.p) + (size_t)M2 * i;
+        I.partial = part + poff * M2;
+        poff += read_tiles[i];
+    }
+    // work list
+    int nw = 0;
+    for (int i : P.tiled) nw = std::max<int>(nw, P.inst[i].N);
+    P.nwaves = nw;
+    const int nt = (int)P.tiled.size();
+    std::vector<int64_t> wave_off(nw + 2, 0), ioff((size_t)(nw + 1) * (nt + 1), 0);
+    std::vector<unsigned> need((size_t)(nw + 1) * std::max(nt, 1), 0), ntl((size_t)(nw + 1) * std::max(nt, 1), 0);
+    wave_off[0] = 0;
+    wave_off[1] = (int64_t)P.resident.size();
+    std::vector<unsigned> cum(nt, 0);
+    for (int n = 1; n <= nw; ++n) {
+        int64_t acc = 0;
+        for (int k = 0; k < nt; ++k) {
+            const BatchInst& I = P.inst[P.tiled[k]];
+            const unsigned t = tiles_at(M2, I.L, I.N, n, te, I.read.n_in);
+            ntl[(size_t)n * nt + k] = t;
+            need[(size_t)n * nt + k] = cum[k];
+            ioff[(size_t)n * (nt + 1) + k] = acc;
+            acc += (t + group - 1) / group;
+            cum[k] += t;
+        }
+        ioff[(size_t)n * (nt + 1) + nt] = acc;
+        wave_off[n + 1] = wave_off[n] + acc;
+    }
+    P.total_items = wave_off[nw + 1];
+    if (nw == 0) P.total_items = wave_off[1];
+    if (const char* f = std::getenv("QUAPI_FAULT")) {
+        // host-side fault injection: the first tiled instance's step 2 waits for a count nothing reaches
+        if (std::strcmp(f, "batch_wait") == 0 && nt > 0 && nw >= 2) need[(size_t)2 * nt + 0] = 0xFFFFFFFFu;
+    }
+    if ((e = upload(P.d_inst, P.inst)) != cudaSuccess) return e;
+    if ((e = upload(P.d_res, P.resident)) != cudaSuccess) return e;
+    if ((e = upload(P.d_tiled, P.tiled)) != cudaSuccess) return e;
+    if ((e = upload(P.d_wave, wave_off)) != cudaSuccess) return e;
+    if ((e = upload(P.d_ioff, ioff)) != cudaSuccess) return e;
+    if ((e = upload(P.d_need, need)) != cudaSuccess) return e;
+    if ((e = upload(P.d_nt, ntl)) != cudaSuccess) return e;
+    BatchArgs& a = P.args;
+    a.inst = static_cast<const BatchInst*>(P.d_inst.p);
+    a.resident = static_cast<const int*>(P.d_res.p);
+    a.nresident = (int)P.resident.size();
+    a.tiled = static_cast<const int*>(P.d_tiled.p);
+    a.ntiled = nt;
+    a.nwaves = nw;
+    a.wave_off = static_cast<const int64_t*>(P.d_wave.p);
+    a.inst_off = static_cast<const int64_t*>(P.d_ioff.p);
+    a.need = static_cast<const unsigned*>(P.d_need.p);
+    a.ntiles = static_cast<const unsigned*>(P.d_nt.p);
+    a.total_items = P.total_items;
+    a.next_item = static_cast<unsigned long long*>(P.d_next.p);
+    a.err = static_cast<int*>(P.d_err.p);
+    a.group = group;
+    a.wait_ns = wait_ns;
+    return cudaSuccess;
+}
+
+std::string signature(const std::vector<BatchInst>& insts, int M, int form) {
+    std::vector<std::pair<int, int64_t>> v;
+    for (const auto& I : insts) v.emplace_back(I.L, (int64_t)I.N);
+    std::sort(v.begin(), v.end());
+    std::ostringstream o;
+    o << "M" << M << "f" << form;
+    for (auto& p : v) o << ";" << p.first << "," << p.second;
+    return o.str();
+}
+
+bool tune_cache_lookup(const std::string& sig, int& fpt, int& group) {
+    auto it = g_tuned.find(sig);
+    if (it != g_tuned.end()) {
+        fpt = it->second.first;
+        group = it->second.second;
+        return true;
+    }
+    const char* path = std::getenv("QUAPI_TUNE_CACHE");
+    if (!path) return false;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string s;
+        int f, g;
+        if (ls >> s >> f >> g && s == sig) {
+            fpt = f;
+            group = g;
+            g_tuned[sig] = {f, g};
+            return true;
+        }
+    }
+    return false;
+}
+
+void tune_cache_store(const std::string& sig, int fpt, int group) {
+    g_tuned[sig] = {fpt, group};
+    if (const char* path = std::getenv("QUAPI_TUNE_CACHE")) {
+        std::ofstream out(path, std::ios::app);
+        out << sig << " " << fpt << " " << group << "\n";
+    }
+}
+
+uint64_t wait_limit_ns() {
+    if (const char* v = std::getenv("QUAPI_WAIT_MS")) {
+        const double ms = std::atof(v);
+        if (ms > 0) return (uint64_t)(ms * 1e6);
+    }
+    return 2000000000ull;
+}
+
+}  // namespace
+
+// Frees every cached batch plan that includes the context with this uid.
+void batch_forget(uint64_t uid) {
+    std::lock_guard<std::mutex> lock(g_plans_mutex);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        Plan* P = it->second;
+        if (std::find(P->uids.begin(), P->uids.end(), uid) != P->uids.end()) {
+            delete P;
+            it = g_plans.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+}  // namespace quapi
+
+using namespace quapi;
+
+extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
+                                              const int64_t* nsteps_each, double* const* rho_final) {
+    if (n < 1 || !ctxs || !rho0s || !nsteps_each || !rho_final)
+        return record_error(nullptr, QUAPI_ERR_ARG, "batch: n >= 1 and non-NULL arrays required");
+    std::vector<BatchInst> insts(n);
+    std::vector<uint64_t> uids(n);
+    std::vector<int64_t> Ns(n);
+    int M0 = 0, form0 = 0, L = 0;
+    cudaStream_t st0 = nullptr;
+    bool tune = false;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !rho0s[i] || !rho_final[i])
+            return record_error(nullptr, QUAPI_ERR_ARG, "batch: NULL context or buffer");
+        if (nsteps_each[i] < 0) return record_error(nullptr, QUAPI_ERR_ARG, "batch: final steps must be >= 0");
+        int M, form;
+        cudaStream_t st;
+        batch_describe(ctxs[i], nsteps_each[i], &insts[i], &M, &form, &st, &L);
+        if (i == 0) {
+            M0 = M;
+            form0 = form;
+            st0 = st;
+        } else if (M != M0 || form != form0) {
+            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: all contexts need the same M and precision");
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
+        uids[i] = ctx_uid(ctxs[i]);
+        Ns[i] = nsteps_each[i];
+    }
+    if (const char* v = std::getenv("QUAPI_TUNE")) tune = std::atoi(v) != 0;
+    tune = tune || ctx_tune_requested(ctxs[0]);
+    const int M2 = M0 * M0;
+    // instances that stop at step 0 return rho0 unchanged and stay out of the kernel
+    std::vector<int> active;
+    for (int i = 0; i < n; ++i) {
+        if (Ns[i] == 0) std::memcpy(rho_final[i], rho0s[i], sizeof(double) * 2 * M2);
+        else active.push_back(i);
+    }
+    if (active.empty()) return QUAPI_OK;
+    std::vector<BatchInst> act;
+    std::vector<uint64_t> auids;
+    std::vector<int64_t> aNs;
+    for (int i : active) {
+        act.push_back(insts[i]);
+        auids.push_back(uids[i]);
+        aNs.push_back(Ns[i]);
+    }
+    const std::string sig = signature(act, M0, form0);
+    const uint64_t wait_ns = wait_limit_ns();
+
+    std::lock_guard<std::mutex> lock(g_plans_mutex);
+    int fpt = form0 == QUAPI_FP32 ? 2 : 1, group = 4;
+    auto get_plan = [&](int f, int g, Plan** out) -> cudaError_t {
+        const std::string key = plan_key(auids, aNs, f, g);
+        auto it = g_plans.find(key);
+        if (it != g_plans.end()) {
+            *out = it->second;
+            return cudaSuccess;
+        }
+        Plan* P = new Plan();
+        P->uids = auids;
+        P->Ns = aNs;
+        cudaError_t e = build_plan(*P, act, M0, form0, f, g, wait_ns);
+        if (e != cudaSuccess) {
+            delete P;
+            return e;
+        }
+        g_plans[key] = P;
+        *out = P;
+        return cudaSuccess;
+    };
+    if (tune && !tune_cache_lookup(sig, fpt, group)) {
+        // time every candidate launch shape once (after a warm-up run) and keep the fastest
+        const int fpts[3] = {1, 2, 4};
+        const int groups[3] = {1, 4, 16};
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (int f : fpts)
+            for (int g : groups) {
+                Plan* P = nullptr;
+                if (get_plan(f, g, &P) != cudaSuccess) continue;
+                for (size_t j = 0; j < active.size(); ++j)
+                    std::memcpy(P->h_rho0 + 2 * M2 * j, rho0s[active[j]], sizeof(double) * 2 * M2);
+                if (enqueue_run(*P, st0) != cudaSuccess) continue;
+                cudaEventRecord(e0, st0);
+                if (enqueue_run(*P, st0) != cudaSuccess) continue;
+                cudaEventRecord(e1, st0);
+                count_launch(4);
+                if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    fpt = f;
+                    group = g;
+                }
+            }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tune_cache_store(sig, fpt, group);
+    }
+    Plan* P = nullptr;
+    cudaError_t e = get_plan(fpt, group, &P);
+    if (e != cudaSuccess)
+        return record_error(nullptr, e == cudaErrorMemoryAllocation ? QUAPI_ERR_OOM : QUAPI_ERR_CUDA,
+                            cudaGetErrorString(e));
+    for (size_t j = 0; j < active.size(); ++j)
+        std::memcpy(P->h_rho0 + 2 * M2 * j, rho0s[active[j]], sizeof(double) * 2 * M2);
+    if (!P->exec) {
+        // capture the whole run (counter resets, copies, both kernels) once; replay it afterwards
+        if ((e = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking)) != cudaSuccess)
+            return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+        if ((e = launch_plan(*P, P->cap, true)) != cudaSuccess)  // attributes and grid, outside the capture
+            return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+        cudaGraph_t graph = nullptr;
+        if ((e = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+        cudaError_t ee = enqueue_run(*P, P->cap);
+        e = cudaStreamEndCapture(P->cap, &graph);
+        if (ee != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(ee != cudaSuccess ? ee : e));
+        }
+        e = cudaGraphInstantiate(&P->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if ((e = cudaGraphLaunch(P->exec, st0)) != cudaSuccess)
+        return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+    count_launch(P->args.ntiled ? 2 : 1);
+    if ((e = cudaStreamSynchronize(st0)) != cudaSuccess)
+        return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+    int flag = 0;
+    cudaMemcpy(&flag, P->d_err.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (flag) {
+        cudaMemset(P->d_err.p, 0, sizeof(int));
+        return record_error(nullptr, QUAPI_ERR_TIMEOUT, "batch: a dependency wait gave up");
+    }
+    for (size_t j = 0; j < active.size(); ++j)
+        std::memcpy(rho_final[active[j]], P->h_rho + 2 * M2 * j, sizeof(double) * 2 * M2);
+    return QUAPI_OK;
+}

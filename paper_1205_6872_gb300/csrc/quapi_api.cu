@@ -73,6 +73,8 @@ struct quapi_ctx {
     int max_grid = 0;
     bool use_tma = true;         // M = 2: TMA-staged step kernel when the tensor allows it
     int stages = 2;              // its ring depth (2 measured best: 4 CTAs per SM fit)
+    bool tune = false;           // quapi_opts.tune
+    uint64_t uid = 0;            // never reused within the process
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
     OpPlan step_first, step_steady, read_steady;
@@ -256,6 +258,11 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     c->endpoint = o.endpoint_mode;
     c->st = reinterpret_cast<cudaStream_t>(o.cuda_stream);
     c->host_s.assign(s, s + M);
+    c->tune = o.tune != 0;
+    {
+        static std::atomic<uint64_t> next_uid{1};
+        c->uid = next_uid.fetch_add(1);
+    }
     auto bail = [&](quapi_status st) {
         std::string m = c->err;
         quapi_destroy(c);
@@ -519,6 +526,45 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     return QUAPI_OK;
 }
 
+OpRef op_ref(const quapi_ctx* c, const OpPlan& p) {
+    OpRef r;
+    r.isum = p.summed ? c->d_tables + p.off_isum : nullptr;
+    r.lo = c->d_tables + p.off_lo;
+    r.hi = c->d_tables + p.off_hi;
+    r.lo_size = p.lo_size;
+    int sh = 0;
+    while ((int64_t(1) << sh) < p.lo_size) ++sh;
+    r.lo_shift = sh;
+    r.hi_size = p.hi_size;
+    r.n_in = p.n_in;
+    r.diag = (p.n_in >= 2 && p.nk > p.j) ? 1 : 0;
+    return r;
+}
+
+quapi_status batch_describe(const quapi_ctx* c, int64_t N, BatchInst* inst, int* M, int* form, cudaStream_t* st,
+                            int* L) {
+    std::memset(inst, 0, sizeof(*inst));
+    inst->buf[0] = c->buf[0];
+    inst->buf[1] = c->buf[1];
+    inst->L = c->L;
+    inst->N = (int)N;
+    inst->self0_idx = eta_self0(c->L);
+    inst->eta = c->d_eta;
+    inst->s = c->d_s;
+    for (int n = 1; n < c->L; ++n) inst->grow[n] = op_ref(c, c->grow_ops[n]);
+    inst->step_first = op_ref(c, c->step_first);
+    inst->step = op_ref(c, c->step_steady);
+    if (N >= 1) inst->read = op_ref(c, N <= c->L ? c->read_ops[N] : c->read_steady);
+    *M = c->M;
+    *form = c->form;
+    *st = c->st;
+    *L = c->L;
+    return QUAPI_OK;
+}
+
+uint64_t ctx_uid(const quapi_ctx* c) { return c->uid; }
+bool ctx_tune_requested(const quapi_ctx* c) { return c->tune; }
+
 quapi_status record_error(const quapi_ctx* c, quapi_status st, const char* msg) {
     return fail(const_cast<quapi_ctx*>(c), st, msg);
 }
@@ -621,16 +667,6 @@ quapi_status quapi_get_propagator(const quapi_ctx* c, double* U_out, double* K_o
     return QUAPI_OK;
 }
 
-quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
-                                   const int64_t* nsteps_each, double* const* rho_final) {
-    (void)n;
-    (void)ctxs;
-    (void)rho0s;
-    (void)nsteps_each;
-    (void)rho_final;
-    return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "batched propagation not built yet");
-}
-
 uint64_t quapi_kernel_launches(void) { return launches_so_far(); }
 
 const char* quapi_last_error(const quapi_ctx* c) {
@@ -640,6 +676,7 @@ const char* quapi_last_error(const quapi_ctx* c) {
 
 void quapi_destroy(quapi_ctx* c) {
     if (!c) return;
+    batch_forget(c->uid);
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
     cudaFree(c->d_s);

@@ -180,3 +180,44 @@ quapi_status readout_launch_args(const ::quapi_ctx* c, int64_t n, const void* A_
                                  int* form, cudaStream_t* st);
 quapi_status record_error(const ::quapi_ctx* c, quapi_status st, const char* msg);
 }  // namespace quapi
+
+namespace quapi {
+
+// One operation's tables inside a context's arena (device pointers).
+struct OpRef {
+    const void* isum = nullptr;
+    const void* lo = nullptr;
+    const void* hi = nullptr;
+    int64_t lo_size = 1;
+    int lo_shift = 0;
+    int64_t hi_size = 1;
+    int n_in = 0;
+    int diag = 0;  // diagonal fast path valid for this operation
+};
+
+// Everything the batched kernel needs about one instance (device-visible copy).
+struct BatchInst {
+    void* buf[2];
+    int L, N, resident;
+    int self0_idx;
+    const double2* eta;
+    const double* s;
+    OpRef grow[kMaxDigits];  // growth step n = 1..L-1 at index n
+    OpRef step_first;        // n == L
+    OpRef step;              // n > L
+    OpRef read;              // readout at n == N
+    double2* partial;        // [readout tiles][M^2]
+    unsigned int* done;      // tiles completed over all steps
+    unsigned int* read_done; // readout tiles completed
+    double2* rho_out;        // M^2 (device)
+    const double2* rho0;     // M^2 (device)
+};
+
+uint64_t ctx_uid(const ::quapi_ctx* c);            // unique per context for the process lifetime
+bool ctx_tune_requested(const ::quapi_ctx* c);     // quapi_opts.tune was set
+void batch_forget(uint64_t uid);                    // drop cached batch plans using that context
+
+// Fill inst with the tables and tensors of context c for a run to step N (host side).
+quapi_status batch_describe(const ::quapi_ctx* c, int64_t N, BatchInst* inst, int* M, int* form, cudaStream_t* st,
+                            int* L);
+}  // namespace quapi
