@@ -128,26 +128,18 @@ class ClockSampler:
 
 
 def dist_setup():
-    world = _env_int("WORLD_SIZE", 1)
-    rank = _env_int("RANK", 0)
-    local = _env_int("LOCAL_RANK", 0)
-    return world, rank, local
+    from paper_1205_6872_gb300 import replicas
+    return replicas.env_ranks()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_1205_6872_gb300 import replicas
+    replicas.barrier()
 
 
 def max_over_ranks(value, world):
-    if world == 1:
-        return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1205_6872_gb300 import replicas
+    return replicas.reduce_max(value)
 
 
 def element_updates(p):
@@ -229,6 +221,61 @@ def time_e2e(q, torch, p, precision, steps, warmup):
     return (time.perf_counter() - t0) / steps
 
 
+def batch_updates(probs):
+    return float(sum((p.M * p.M) ** p.L * max(p.N - p.L + 1, 0) for p in probs))
+
+
+def time_batched(q, torch, steps, warmup, world, rank):
+    """256 spin-boson instances: one batched FP32 launch (autotuned, graph replay) vs the
+    same instances solved one after another with the plain FP64 propagator.  Under N ranks
+    each rank takes a contiguous shard of the instances."""
+    from paper_1205_6872_gb300 import replicas
+    from paper_1205_6872_gb300 import workloads as wl
+    allp = wl.batched_256()
+    a, b = replicas.shard(len(allp), rank, world)
+    probs = allp[a:b]
+    ups = batch_updates(probs)
+    c32 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                         q.quapi_opts_init(precision=q.QUAPI_FP32, tune=1)) for p in probs]
+    try:
+        rho0s = [p.rho0 for p in probs]
+        Ns = [p.N for p in probs]
+        for _ in range(max(warmup, 1)):
+            q.quapi_propagate_batch(c32, rho0s, Ns)  # first call tunes and captures the graph
+        torch.cuda.synchronize()
+        replicas.barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r32 = q.quapi_propagate_batch(c32, rho0s, Ns)
+        batched_s = replicas.reduce_max((time.perf_counter() - t0) / steps)
+    finally:
+        for c in c32:
+            q.quapi_destroy(c)
+    c64 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                         q.quapi_opts_init(precision=q.QUAPI_FP64)) for p in probs]
+    try:
+        rho0 = torch.tensor(np.asarray(probs[0].rho0).reshape(-1), dtype=torch.complex128, device="cuda")
+        outs = torch.empty((len(probs), 4), dtype=torch.complex128, device="cuda")
+        for c, p, i in zip(c64, probs, range(len(probs))):
+            q.quapi_propagate_device(c, rho0, [p.N], outs[i])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, p, i in zip(c64, probs, range(len(probs))):
+            q.quapi_propagate_device(c, rho0, [p.N], outs[i])
+        torch.cuda.synchronize()
+        seq_s = replicas.reduce_max(time.perf_counter() - t0)
+        r64 = outs.cpu().numpy().reshape(-1, 2, 2)
+    finally:
+        for c in c64:
+            q.quapi_destroy(c)
+    diff = replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32, r64)))
+    total = replicas.reduce_sum(ups)
+    return dict(workload="batched_256", instances=len(allp), value=total / batched_s, unit=UNIT,
+                ms_per_batch=1000.0 * batched_s, sequential_fp64_ms=1000.0 * seq_s,
+                sequential_fp64_value=total / seq_s, speedup_vs_sequential_fp64=seq_s / batched_s,
+                fp32_vs_fp64_max_abs=diff)
+
+
 def cpu_oracle_sample(p, nsteps):
     """The FP64 oracle's steady-state step on a full-size tensor, nsteps times (host cores)."""
     import oracle
@@ -281,7 +328,7 @@ def run_kernel_only(args):
     torch.cuda.set_device(0)
     p = wl.spin_boson_L14()
     L = args.dkmax
-    prec = q.QUAPI_FP32 if args.form == "fp32" else q.QUAPI_FP64
+    prec = {"fp32": q.QUAPI_FP32, "fp64": q.QUAPI_FP64, "df64": q.QUAPI_DF64}[args.form]
     tbytes, _ = q.quapi_query_memory(p.M, L, prec)
     ws = torch.empty(tbytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
@@ -319,10 +366,11 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused steady-state step kernel (profiling case)")
     ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
-    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64"], help="form for --kernel-only")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"], help="form for --kernel-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -353,6 +401,8 @@ def main():
                                                                     for z in r64["rho"].reshape(-1)])
         forms["fp64"]["fp32_vs_fp64_max_abs"] = float(np.abs(r32["rho"] - r64["rho"]).max())
         forms["fp64"]["speedup_fp32_over_fp64"] = r64["ms"] / r32["ms"]
+    if not args.no_batched:
+        forms["batched_256_fp32"] = time_batched(q, torch, args.steps, args.warmup, world, rank)
     e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1))
     e2e_s = max_over_ranks(e2e_s, world)
     peak, peak_kind = measured_peaks()

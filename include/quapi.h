@@ -18,7 +18,8 @@
  *   - The augmented tensor A (device) has (M^2)^L complex entries; digit p of
  *     its flat index (base M^2, p = 0 least significant) holds the path point
  *     k - L + 1 + p, so the oldest point is contiguous.  FP64 form: complex
- *     double (16 B); FP32 form: complex float (8 B).
+ *     double (16 B); FP32 form: complex float (8 B); DF64 form: four floats
+ *     {re_hi, im_hi, re_lo, im_lo} (16 B) with value (re_hi + re_lo) + i (im_hi + im_lo).
  *   - The caller owns every host array it passes; the library copies what it
  *     needs and keeps no caller pointer beyond the call.  Device memory that
  *     the library allocates is owned by the context and released by
@@ -63,8 +64,12 @@ typedef struct {
 
 enum {
     QUAPI_FP64 = 64,  /* tensor stored and propagated in complex double */
-    QUAPI_FP32 = 32   /* complex float storage and products; double-float tables,
+    QUAPI_FP32 = 32,  /* complex float storage and products; double-float tables,
                          compensated index sums, FP64 eta / K / readout */
+    QUAPI_DF64 = 48   /* FP64-equivalent form on the FP32 pipes: each entry stored as a
+                         double-float pair (hi + lo floats, 16 B per complex entry, ~48-bit
+                         significands), triple-float tables holding the FP64 values exactly,
+                         error-free products and sums; FP64 readout */
 };
 
 enum {
@@ -74,7 +79,7 @@ enum {
 };
 
 typedef struct {
-    int precision;          /* QUAPI_FP64 (default) or QUAPI_FP32                                  */
+    int precision;          /* QUAPI_FP64 (default), QUAPI_FP32 or QUAPI_DF64                      */
     int endpoint_mode;      /* QUAPI_ENDPOINT_STRANG (default) or QUAPI_ENDPOINT_INTERIOR           */
     void* cuda_stream;      /* cudaStream_t all work is issued on; NULL = the legacy default stream */
     int tune;               /* 0: default launch shape; 1: pick it by timing candidates (cached)   */

@@ -42,6 +42,11 @@ template <> struct FormT<QUAPI_FP32> {
     using Tab = ff2;
     static constexpr int FPT = 2;
 };
+template <> struct FormT<QUAPI_DF64> {
+    using Elem = df2;
+    using Tab = tf2;
+    static constexpr int FPT = 1;
+};
 
 template <int M> __device__ __forceinline__ constexpr bool is_diag(int x) { return (x / M) == (x % M); }
 
@@ -63,8 +68,22 @@ template <int M> struct Split {
 __device__ __forceinline__ double2 tmul(const double2& T, double2 v) { return cmul(T, v); }
 __device__ __forceinline__ float2 tmul(const ff2& T, float2 v) { return ffmul(T, v); }
 
+__device__ __forceinline__ df2 tmul(const tf2& T, df2 v) { return tfmul(T, v); }
+
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
 __device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ df2 ld_stream(const df2* p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    df2 r;
+    r.h = make_float2(v.x, v.y);
+    r.l = make_float2(v.z, v.w);
+    return r;
+}
+__device__ __forceinline__ void st_stream(double2* p, double2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(float2* p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(df2* p, df2 v) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v.h.x, v.h.y, v.l.x, v.l.y));
+}
 
 // Loads the FPT fibers of this thread (valid[u] says whether fiber u exists).
 template <int M2, int FORM>
@@ -113,7 +132,7 @@ __device__ __forceinline__ void store_row(typename FormT<FORM>::Elem* __restrict
     }
 #pragma unroll
     for (int u = 0; u < FPT; ++u)
-        if (valid[u]) __stcs(out + idx + u, v[u]);
+        if (valid[u]) st_stream(out + idx + u, v[u]);
 }
 
 // Readout accumulators: FP64 form in double, FP32 form compensated in float.
@@ -130,6 +149,15 @@ template <> struct RhoAcc<QUAPI_FP32> {
     __device__ __forceinline__ void add(float2 v) { a.add(v); }
     __device__ __forceinline__ double2 value() const {
         return make_double2((double)a.s.x + (double)a.c.x, (double)a.s.y + (double)a.c.y);
+    }
+};
+
+template <> struct RhoAcc<QUAPI_DF64> {
+    df2 a;
+    __device__ __forceinline__ void init() { a.h = a.l = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ void add(df2 v) { a = dfadd(a, v); }
+    __device__ __forceinline__ double2 value() const {
+        return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
     }
 };
 
@@ -163,6 +191,20 @@ template <int M2> __device__ __forceinline__ kahan32 plain_sum(const float2 (&a)
     return acc;
 }
 
+template <int M2>
+__device__ __forceinline__ df2 row_sum(const tf2* __restrict__ isum_row, const df2 (&a)[M2]) {
+    df2 s = tfmul(isum_row[0], a[0]);
+#pragma unroll
+    for (int q = 1; q < M2; ++q) s = dfadd(s, tfmul(isum_row[q], a[q]));
+    return s;
+}
+template <int M2> __device__ __forceinline__ df2 plain_sum(const df2 (&a)[M2]) {
+    df2 s = a[0];
+#pragma unroll
+    for (int q = 1; q < M2; ++q) s = dfadd(s, a[q]);
+    return s;
+}
+
 // hi * (lo * S)
 __device__ __forceinline__ double2 apply_p(const double2& hi, const double2& lo, double2 S) {
     return cmul(hi, cmul(lo, S));
@@ -170,7 +212,11 @@ __device__ __forceinline__ double2 apply_p(const double2& hi, const double2& lo,
 __device__ __forceinline__ float2 apply_p(const ff2& hi, const ff2& lo, const kahan32& S) {
     return ffmul(hi, ffmul2(lo, S.s, S.c));
 }
+__device__ __forceinline__ df2 apply_p(const tf2& hi, const tf2& lo, const df2& S) {
+    return tfmul(hi, tfmul(lo, S));
+}
 __device__ __forceinline__ double2 apply_hi(const double2& hi, double2 S) { return cmul(hi, S); }
+__device__ __forceinline__ df2 apply_hi(const tf2& hi, const df2& S) { return tfmul(hi, S); }
 __device__ __forceinline__ float2 apply_hi(const ff2& hi, const kahan32& S) { return ffmul2(hi, S.s, S.c); }
 
 // Tables of one launch: summed-digit and lo tables staged in shared memory,
@@ -456,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
                     a[e0 / M2][e0 % M2] = make_float2(v.x, v.y);
                     a[e1 / M2][e1 % M2] = make_float2(v.z, v.w);
                 } else {
-                    a[0][q] = *reinterpret_cast<const double2*>(row + pos * 16);
+                    a[0][q] = *reinterpret_cast<const Elem*>(row + pos * 16);  // one complex entry per chunk
                 }
             }
         }
@@ -616,7 +662,7 @@ cudaError_t launch_step_mf(StepArgs& a, cudaStream_t st) {
     const bool W = a.A_out != nullptr, R = a.partial != nullptr;
     if constexpr (M == 2) if (a.use_tma && a.diag_fast) {
         constexpr int FPT = FormT<FORM>::FPT;
-        const int64_t elt = (FORM == QUAPI_FP64) ? 16 : 8;
+        const int64_t elt = (FORM == QUAPI_FP32) ? 8 : 16;
         CUtensorMap map;
         if (a.F % ((int64_t)kThreads * FPT) == 0 && encode_rows_map(&map, a.A_in, a.F * M * M * elt)) {
             if (W && R) return launch_tma_stages<FORM, true, true, true>(a, map, st);
@@ -654,6 +700,8 @@ cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st) {
     if (M == 2 && form == QUAPI_FP32) return launch_step_mf<2, QUAPI_FP32>(a, st);
     if (M == 3 && form == QUAPI_FP64) return launch_step_mf<3, QUAPI_FP64>(a, st);
     if (M == 3 && form == QUAPI_FP32) return launch_step_mf<3, QUAPI_FP32>(a, st);
+    if (M == 2 && form == QUAPI_DF64) return launch_step_mf<2, QUAPI_DF64>(a, st);
+    if (M == 3 && form == QUAPI_DF64) return launch_step_mf<3, QUAPI_DF64>(a, st);
     return cudaErrorInvalidValue;
 }
 
@@ -667,6 +715,8 @@ cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t 
     else if (M == 2 && form == QUAPI_FP32) QUAPI_GROW(2, QUAPI_FP32);
     else if (M == 3 && form == QUAPI_FP64) QUAPI_GROW(3, QUAPI_FP64);
     else if (M == 3 && form == QUAPI_FP32) QUAPI_GROW(3, QUAPI_FP32);
+    else if (M == 2 && form == QUAPI_DF64) QUAPI_GROW(2, QUAPI_DF64);
+    else if (M == 3 && form == QUAPI_DF64) QUAPI_GROW(3, QUAPI_DF64);
     else return cudaErrorInvalidValue;
 #undef QUAPI_GROW
     count_launch();

@@ -101,7 +101,9 @@ quapi_status cuda_fail(quapi_ctx* c, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return cuda_fail((c), e_, (what)); \
     } while (0)
 
-size_t elem_bytes(int form) { return form == QUAPI_FP64 ? 16 : 8; }
+size_t elem_bytes(int form) { return form == QUAPI_FP32 ? 8 : 16; }
+size_t table_entry_bytes(int form) { return form == QUAPI_DF64 ? 32 : 16; }
+bool valid_precision(int p) { return p == QUAPI_FP64 || p == QUAPI_FP32 || p == QUAPI_DF64; }
 
 // Plan of one operation on an input tensor of n_in digits.
 OpPlan make_plan(int M, int kind, int n_in, bool summed, const int* eta_idx, int self_idx) {
@@ -145,8 +147,8 @@ OpPlan plan_readout(int M, int L, int64_t N, int endpoint) {
     return make_plan(M, OP_READ, n_in, true, idx, self);
 }
 
-size_t plan_bytes(const OpPlan& p, int M2) {
-    const size_t e = 16;  // double2 or ff2
+size_t plan_bytes(const OpPlan& p, int M2, int form) {
+    const size_t e = table_entry_bytes(form);
     size_t b = 0;
     if (p.summed) b += (size_t)M2 * M2 * e;
     b += (size_t)M2 * p.lo_size * e;
@@ -154,8 +156,8 @@ size_t plan_bytes(const OpPlan& p, int M2) {
     return b;
 }
 
-void assign_offsets(OpPlan& p, int M2, size_t& cursor) {
-    const size_t e = 16;
+void assign_offsets(OpPlan& p, int M2, int form, size_t& cursor) {
+    const size_t e = table_entry_bytes(form);
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
     cursor = align(cursor);
     p.off_isum = cursor;
@@ -189,7 +191,7 @@ void make_all_plans(quapi_ctx* c) {
     c->read_steady = plan_readout(c->M, c->L, c->L + 1, c->endpoint);
 }
 
-size_t tables_bytes_for(int M, int L, int endpoint) {
+size_t tables_bytes_for(int M, int L, int endpoint, int form) {
     quapi_ctx tmp;
     tmp.M = M;
     tmp.M2 = M * M;
@@ -197,7 +199,7 @@ size_t tables_bytes_for(int M, int L, int endpoint) {
     tmp.endpoint = endpoint;
     make_all_plans(&tmp);
     size_t cursor = 0;
-    for (OpPlan* p : all_plans(&tmp)) assign_offsets(*p, tmp.M2, cursor);
+    for (OpPlan* p : all_plans(&tmp)) assign_offsets(*p, tmp.M2, form, cursor);
     return cursor + 256;
 }
 
@@ -217,8 +219,8 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
                 return fail(nullptr, QUAPI_ERR_ARG, "H must be Hermitian (tolerance 1e-12)");
         }
     if (o) {
-        if (o->precision != QUAPI_FP64 && o->precision != QUAPI_FP32)
-            return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64 or QUAPI_FP32");
+        if (!valid_precision(o->precision))
+            return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64, QUAPI_FP32 or QUAPI_DF64");
         if (o->endpoint_mode != QUAPI_ENDPOINT_STRANG && o->endpoint_mode != QUAPI_ENDPOINT_INTERIOR)
             return fail(nullptr, QUAPI_ERR_ARG, "unknown endpoint_mode");
     }
@@ -292,7 +294,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     }
     make_all_plans(c);
     size_t cursor = 0;
-    for (OpPlan* p : all_plans(c)) assign_offsets(*p, M2, cursor);
+    for (OpPlan* p : all_plans(c)) assign_offsets(*p, M2, c->form, cursor);
     SCHECK(cudaMalloc(&c->d_tables, cursor + 256), "cudaMalloc(tables)");
     c->max_grid = num_sms() * 8;  // at most 8 resident CTAs of 256 threads per SM
     SCHECK(cudaMalloc(&c->d_partial, sizeof(double2) * M2 * (size_t)c->max_grid), "cudaMalloc(partials)");
@@ -584,12 +586,12 @@ quapi_status quapi_query_memory(int M, int dkmax, int precision, size_t* tensor_
     if (!tensor_bytes && !total_bytes) return fail(nullptr, QUAPI_ERR_ARG, "no output pointer");
     if (M != 2 && M != 3) return fail(nullptr, QUAPI_ERR_ARG, "M must be 2 or 3");
     if (dkmax < 1 || dkmax > max_dkmax(M)) return fail(nullptr, QUAPI_ERR_ARG, "dkmax out of range");
-    if (precision != QUAPI_FP64 && precision != QUAPI_FP32)
-        return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64 or QUAPI_FP32");
+    if (!valid_precision(precision))
+        return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64, QUAPI_FP32 or QUAPI_DF64");
     const size_t t = 2 * (size_t)ipow(M * M, dkmax) * elem_bytes(precision);
     if (tensor_bytes) *tensor_bytes = t;
     if (total_bytes) {
-        size_t tb = tables_bytes_for(M, dkmax, QUAPI_ENDPOINT_STRANG);
+        size_t tb = tables_bytes_for(M, dkmax, QUAPI_ENDPOINT_STRANG, precision);
         *total_bytes = t + tb + (size_t)16 * M * M * 152 * 16 + 4096;
     }
     return QUAPI_OK;

@@ -90,6 +90,74 @@ struct kahan32 {
 };
 
 // ---------------------------------------------------------------------------
+// Double-float form (QUAPI_DF64): a complex entry is two complex floats whose
+// sum carries ~48 significant bits per component; tables are triple floats
+// (t1 + t2 + t3 holds the FP64 master value exactly).  All arithmetic runs on
+// the FP32 pipes with error-free transformations (TwoProd by FMA, TwoSum).
+// ---------------------------------------------------------------------------
+struct __align__(16) df2 {
+    float2 h, l;  // value = h + l per component
+};
+struct __align__(16) tf2 {
+    float2 t1, t2, t3, pad;
+};
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+    s = a + b;
+    e = b - (s - a);
+}
+
+// one real component of T * x:  T.t1 x.h exactly (TwoProd) plus the small cross terms
+__device__ __forceinline__ void tf_dot_part(float t1, float t2, float t3, float xh, float xl, float& p, float& e) {
+    p = t1 * xh;
+    e = fmaf(t1, xh, -p);
+    e = fmaf(t1, xl, e);
+    e = fmaf(t2, xh, e);
+    e = fmaf(t2, xl, e);
+    e = fmaf(t3, xh, e);
+}
+
+// (p1 + e1) - (p2 + e2) renormalised to a double-float
+__device__ __forceinline__ void df_diff(float p1, float e1, float p2, float e2, float& h, float& l) {
+    float s, t;
+    two_sum(p1, -p2, s, t);
+    t += e1 - e2;
+    fast_two_sum(s, t, h, l);
+}
+__device__ __forceinline__ void df_sum2(float p1, float e1, float p2, float e2, float& h, float& l) {
+    float s, t;
+    two_sum(p1, p2, s, t);
+    t += e1 + e2;
+    fast_two_sum(s, t, h, l);
+}
+
+// T * x for a triple-float table entry T and a double-float complex x
+__device__ __forceinline__ df2 tfmul(const tf2& T, const df2& x) {
+    float pa, ea, pb, eb, pc, ec, pd, ed;
+    tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.x, x.l.x, pa, ea);  // Tre * xre
+    tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.y, x.l.y, pb, eb);  // Tim * xim
+    tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.y, x.l.y, pc, ec);  // Tre * xim
+    tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.x, x.l.x, pd, ed);  // Tim * xre
+    df2 r;
+    df_diff(pa, ea, pb, eb, r.h.x, r.l.x);
+    df_sum2(pc, ec, pd, ed, r.h.y, r.l.y);
+    return r;
+}
+
+// x + y for double-float complex values (TwoSum on the high parts)
+__device__ __forceinline__ df2 dfadd(const df2& x, const df2& y) {
+    df2 r;
+    float s, t;
+    two_sum(x.h.x, y.h.x, s, t);
+    t += x.l.x + y.l.x;
+    fast_two_sum(s, t, r.h.x, r.l.x);
+    two_sum(x.h.y, y.h.y, s, t);
+    t += x.l.y + y.l.y;
+    fast_two_sum(s, t, r.h.y, r.l.y);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side description of one tensor operation (growth, step or readout).
 // ---------------------------------------------------------------------------
 enum OpKind { OP_GROW = 0, OP_STEP = 1, OP_READ = 2 };

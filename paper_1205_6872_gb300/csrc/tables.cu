@@ -106,6 +106,11 @@ __global__ void init_tensor_kernel(const double2* __restrict__ rho0, const doubl
     double2 v = cmul(rho0[x], cexp_d(z));
     if (form == QUAPI_FP64) {
         reinterpret_cast<double2*>(A_out)[x] = v;
+    } else if (form == QUAPI_DF64) {
+        df2 r;
+        r.h = make_float2((float)v.x, (float)v.y);
+        r.l = make_float2((float)(v.x - (double)r.h.x), (float)(v.y - (double)r.h.y));
+        reinterpret_cast<df2*>(A_out)[x] = r;
     } else {
         reinterpret_cast<float2*>(A_out)[x] = make_float2((float)v.x, (float)v.y);
     }
@@ -114,6 +119,15 @@ __global__ void init_tensor_kernel(const double2* __restrict__ rho0, const doubl
 __device__ __forceinline__ void store_entry(void* base, int64_t idx, int form, double2 v) {
     if (form == QUAPI_FP64) {
         reinterpret_cast<double2*>(base)[idx] = v;
+    } else if (form == QUAPI_DF64) {
+        // three floats per component: t1 + t2 + t3 reproduces the double v
+        tf2 t;
+        t.t1 = make_float2((float)v.x, (float)v.y);
+        const double rx = v.x - (double)t.t1.x, ry = v.y - (double)t.t1.y;
+        t.t2 = make_float2((float)rx, (float)ry);
+        t.t3 = make_float2((float)(rx - (double)t.t2.x), (float)(ry - (double)t.t2.y));
+        t.pad = make_float2(0.f, 0.f);
+        reinterpret_cast<tf2*>(base)[idx] = t;
     } else {
         ff2 t;
         t.hr = (float)v.x;

@@ -31,6 +31,7 @@ QUAPI_J_OHMIC_EXP = 0
 QUAPI_J_SUPEROHMIC_GAUSS = 1
 QUAPI_FP64 = 64
 QUAPI_FP32 = 32
+QUAPI_DF64 = 48
 QUAPI_ENDPOINT_STRANG = 0
 QUAPI_ENDPOINT_INTERIOR = 1
 

@@ -22,6 +22,13 @@ Workloads (hbar = k_B = 1):
                       H=[[eps,1],[1,-eps]], Ohmic, dt=0.25, 200 steps each, rho0=|0><0|.
 * ``spin_boson_L14``  M=2, H=[[0,1],[1,0]], Ohmic alpha=0.5, wc=2.5, beta=0.5, dt=0.15,
                       Delta k_max=14 (4^14 = 268 M entries), 1000 steps, rho0=|0><0|.
+* ``quantum_dot``     the model system of Sec. III (driven quantum dot after the rotating-wave
+                      approximation): s in {0, 1}, H = (1/2)[[0, W],[W, 0]] with W = pi/8 ps^-1,
+                      J = A w^3 exp(-(w/wc)^2) with A = pi 0.027 ps^2 and wc = 2.2 ps^-1, T = 25 K
+                      (beta = hbar/(k_B T) = 0.6582119569 meV ps / (0.08617333262 meV/K x 25 K) in ps),
+                      Delta k_max = 11; time unit ps.  The paper does not state dt; 0.25 ps is used.
+* ``pulse_area_sweep`` the same dot driven with W_j = theta_j / t_final for pulse areas
+                      theta_j = 5 pi j / n (j = 1..n): rho at t_final only, one instance per area.
 """
 
 from __future__ import annotations
@@ -128,6 +135,24 @@ def random_eta(L: int, seed: int, scale: float = 0.05) -> np.ndarray:
     """A random 4L+3 eta vector (complex), for checks that do not need a physical bath."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return scale * (rng.normal(size=4 * L + 3) + 1j * rng.normal(size=4 * L + 3))
+
+
+HBAR_MEV_PS = 0.6582119569
+KB_MEV_PER_K = 0.08617333262
+
+
+def quantum_dot(L: int = 11, N: int = 1000, dt: float = 0.25, omega: float = np.pi / 8,
+                temperature_K: float = 25.0, name: str = "quantum_dot") -> Problem:
+    beta = HBAR_MEV_PS / (KB_MEV_PER_K * temperature_K)
+    H = 0.5 * np.array([[0.0, omega], [omega, 0.0]], dtype=np.complex128)
+    return Problem(name, np.array([0.0, 1.0]), H, SUPEROHMIC_GAUSS, np.pi * 0.027, 2.2, beta, dt, L, N,
+                   _pure0(2))
+
+
+def pulse_area_sweep(n: int = 64, L: int = 11, N: int = 200, dt: float = 0.25):
+    t_final = N * dt
+    return [quantum_dot(L=L, N=N, dt=dt, omega=5.0 * np.pi * (j + 1) / n / t_final, name=f"pulse_area_{j}")
+            for j in range(n)]
 
 
 CONFIGS = {

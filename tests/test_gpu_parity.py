@@ -86,10 +86,48 @@ def test_propagator_matches_oracle(q, M):
 
 # ---------------------------------------------------------------- single steps on random tensors
 
+def to_df(a):
+    """complex128 -> double-float layout {re_hi, im_hi, re_lo, im_lo} (float32 x 4 per entry)."""
+    a = np.asarray(a, dtype=np.complex128)
+    h = a.astype(np.complex64)
+    l = (a - h.astype(np.complex128)).astype(np.complex64)
+    out = np.empty((a.size, 4), dtype=np.float32)
+    out[:, 0], out[:, 1], out[:, 2], out[:, 3] = h.real, h.imag, l.real, l.imag
+    return out
+
+
+def from_df(x):
+    x = np.asarray(x, dtype=np.float32).reshape(-1, 4).astype(np.float64)
+    return (x[:, 0] + x[:, 2]) + 1j * (x[:, 1] + x[:, 3])
+
+
+def representable(A, prec):
+    """The values the device form stores for A (what both sides must start from)."""
+    if prec == 32:
+        return A.astype(np.complex64).astype(np.complex128)
+    if prec == 48:
+        return from_df(to_df(A))
+    return A
+
+
 def _to_dev(a, prec):
+    if prec == 48:
+        return torch.from_numpy(to_df(a)).cuda()
     t = torch.from_numpy(np.ascontiguousarray(a))
     t = t.to(torch.complex128 if prec == 64 else torch.complex64)
     return t.cuda()
+
+
+def _from_dev(t, prec):
+    if prec == 48:
+        return from_df(t.cpu().numpy())
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def _empty_dev(n, prec):
+    if prec == 48:
+        return torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    return torch.empty(n, dtype=torch.complex128 if prec == 64 else torch.complex64, device="cuda")
 
 
 STEP_CASES = [
@@ -100,7 +138,7 @@ STEP_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 48])
 @pytest.mark.parametrize("M,L,n", STEP_CASES)
 def test_single_step_random_tensor(q, M, L, n, prec):
     pr = _problem(M)
@@ -109,9 +147,7 @@ def test_single_step_random_tensor(q, M, L, n, prec):
     K = oracle.pair_propagator_K(oracle.propagator_U(pr["H"], pr["dt"]))
     M2 = M * M
     n_in = min(n, L)
-    A = wl.random_tensor(M2 ** n_in, seed=7 * n + L)
-    if prec == 32:
-        A = A.astype(np.complex64).astype(np.complex128)  # both sides see the same FP32 input
+    A = representable(wl.random_tensor(M2 ** n_in, seed=7 * n + L), prec)  # both sides start equal
     G, g, n_in_o, summed = rec.step_tables(etad, pr["s"], K, L, n)
     want = rec.apply_step(A, G, g, n_in_o, summed)
     Gr, gr, _ = rec.readout_tables(etad, pr["s"], K, L, n)
@@ -119,20 +155,20 @@ def test_single_step_random_tensor(q, M, L, n, prec):
     ctx = _ctx(q, pr, L, prec, eta=eta)
     try:
         dA = _to_dev(A, prec)
-        dout = torch.empty(want.size, dtype=dA.dtype, device="cuda")
+        dout = _empty_dev(want.size, prec)
         drho = torch.zeros(M2, dtype=torch.complex128, device="cuda")
         q.quapi_step_device(ctx, n, dA, dout, drho)
         torch.cuda.synchronize()
-        got = dout.cpu().numpy().astype(np.complex128)
+        got = _from_dev(dout, prec)
         got_rho = drho.cpu().numpy()
     finally:
         q.quapi_destroy(ctx)
     # element scale: |T| * sum |A| over the summed index
     scale = np.abs(want).max() + 1.0
-    tol = 1e-13 if prec == 64 else 2e-6
+    tol = 2e-6 if prec == 32 else 1e-13
     assert np.abs(got - want).max() <= tol * scale, np.abs(got - want).max()
     rscale = np.abs(A).sum() * np.abs(G).max() ** n_in
-    rtol = 1e-13 if prec == 64 else 1e-6
+    rtol = 1e-6 if prec == 32 else 1e-13
     assert np.abs(got_rho - want_rho).max() <= rtol * max(1.0, np.abs(want_rho).max()) + 1e-15 * rscale
 
 
@@ -155,21 +191,22 @@ def test_spin_boson_L6_fp64_all_steps(q, endpoint):
     assert err <= 1e-12, err
 
 
-def test_spin_boson_L6_fp32_all_steps(q):
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (48, 1e-12)])
+def test_spin_boson_L6_reduced_forms_all_steps(q, prec, tol):
     p = wl.spin_boson_L6()
     spec = Spectral(p.jkind, p.ja, p.wc)
     steps = list(range(p.N + 1))
     want = oracle.propagate(p.s, p.H, spec, p.beta, p.dt, p.L, p.rho0, steps)
-    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(precision=32))
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(precision=prec))
     try:
         got = q.quapi_propagate(ctx, p.rho0, steps, p.M)
     finally:
         q.quapi_destroy(ctx)
     err = max(np.abs(got[i] - want[k]).max() for i, k in enumerate(steps))
-    assert err <= 1e-5, err
+    assert err <= tol, err
 
 
-@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5), (48, 1e-12)])
 @pytest.mark.parametrize("M,L,N", [(2, 1, 30), (2, 3, 2), (2, 8, 60), (3, 3, 25), (3, 5, 12)])
 def test_small_propagations(q, M, L, N, prec, tol):
     pr = _problem(M, seed=5)

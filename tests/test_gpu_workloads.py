@@ -16,12 +16,13 @@ import oracle
 import oracle.recurrence as rec
 from oracle.eta import Spectral
 from paper_1205_6872_gb300 import workloads as wl
+from test_gpu_parity import _empty_dev, _from_dev, _to_dev, representable
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 HERE = os.path.dirname(os.path.abspath(__file__))
 
-TOL = {64: 1e-12, 32: 1e-5}
+TOL = {64: 1e-12, 32: 1e-5, 48: 1e-12}
 
 
 def _golden(name):
@@ -44,7 +45,7 @@ def q():
     return quapi
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 48])
 @pytest.mark.parametrize("name", ["biased_L12", "three_level_L8", "spin_boson_L14"])
 def test_workload_against_stored_oracle(q, name, prec):
     p = wl.CONFIGS[name]()
@@ -82,7 +83,7 @@ def test_batched_instances_sequential(q, prec):
     assert worst <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 48])
 @pytest.mark.parametrize("n", [13, 14, 15])
 def test_full_size_step_sampled(q, prec, n):
     """Growth into the full tensor (n = 13), the first summing step (n = 14), a steady step (n = 15)."""
@@ -92,30 +93,27 @@ def test_full_size_step_sampled(q, prec, n):
     etad = oracle.unpack_eta(eta, L)
     K = oracle.pair_propagator_K(oracle.propagator_U(p.H, p.dt))
     n_in = min(n, L)
-    A = wl.random_tensor(M2 ** n_in, seed=n)
-    if prec == 32:
-        A = A.astype(np.complex64)
+    A = representable(wl.random_tensor(M2 ** n_in, seed=n), prec)
     G, gg, n_in_o, summed = rec.step_tables(etad, p.s, K, L, n)
-    out_size = M2 ** (n_in + (0 if summed else 1) - (1 if summed else 0))
     out_size = M2 ** n_in if summed else M2 ** (n_in + 1)
     ctx = q.quapi_setup_eta(p.s, p.H, eta, p.dt, L, q.quapi_opts_init(precision=prec))
     try:
-        dA = torch.from_numpy(A).cuda()
-        dout = torch.empty(out_size, dtype=dA.dtype, device="cuda")
+        dA = _to_dev(A, prec)
+        dout = _empty_dev(out_size, prec)
         q.quapi_step_device(ctx, n, dA, dout, None)
         torch.cuda.synchronize()
         rng = np.random.Generator(np.random.PCG64(5))
         idx = np.concatenate([np.arange(64), out_size - 1 - np.arange(64), rng.integers(0, out_size, 2048)])
-        got = dout[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.complex128)
+        got = _from_dev(dout[torch.from_numpy(idx).cuda()], prec)
     finally:
         q.quapi_destroy(ctx)
-    want = rec.step_elements(A.astype(np.complex128), G, gg, n_in_o, summed, idx)
+    want = rec.step_elements(A, G, gg, n_in_o, summed, idx)
     scale = np.abs(want).max() + 1.0
-    tol = 1e-13 if prec == 64 else 2e-6
+    tol = 2e-6 if prec == 32 else 1e-13
     assert np.abs(got - want).max() <= tol * scale
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec", [64, 32, 48])
 def test_full_size_readout(q, prec):
     """rho read out of a random 4^14-entry tensor (steady state, end-point tables) vs the oracle."""
     p = wl.spin_boson_L14()
@@ -123,13 +121,11 @@ def test_full_size_readout(q, prec):
     eta = oracle.pack_eta(oracle.eta_table(Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, L))
     etad = oracle.unpack_eta(eta, L)
     K = oracle.pair_propagator_K(oracle.propagator_U(p.H, p.dt))
-    A = wl.random_tensor(M2 ** L, seed=21)
-    if prec == 32:
-        A = A.astype(np.complex64)
+    A = representable(wl.random_tensor(M2 ** L, seed=21), prec)
     n = L + 3
     ctx = q.quapi_setup_eta(p.s, p.H, eta, p.dt, L, q.quapi_opts_init(precision=prec))
     try:
-        dA = torch.from_numpy(A).cuda()
+        dA = _to_dev(A, prec)
         rho = torch.zeros(M2, dtype=torch.complex128, device="cuda")
         q.quapi_step_device(ctx, n, dA, None, rho)
         torch.cuda.synchronize()
@@ -138,10 +134,10 @@ def test_full_size_readout(q, prec):
         q.quapi_destroy(ctx)
         del dA
     Gr, gr, n_in = rec.readout_tables(etad, p.s, K, L, n)
-    want = rec.apply_readout(A.astype(np.complex128), Gr, gr, n_in)
+    want = rec.apply_readout(A, Gr, gr, n_in)
     # random-sign sum of 4^15 terms: relative rounding error ~ eps * sqrt(#terms) of the term scale
-    term = np.sqrt(np.mean(np.abs(A.astype(np.complex128)) ** 2))
-    tol = (1e-12 if prec == 64 else 1e-5) * term * np.sqrt(M2 ** (L + 1)) + 1e-12 * np.abs(want).max()
+    term = np.sqrt(np.mean(np.abs(A) ** 2))
+    tol = (1e-6 if prec == 32 else 1e-14) * term * np.sqrt(M2 ** (L + 1)) + 1e-12 * np.abs(want).max()
     assert np.abs(got - want).max() <= tol, (got, want)
 
 
