@@ -358,13 +358,40 @@ def run_kernel_only(args):
     return 0
 
 
+def run_batched_only(args):
+    """One batched FP32 launch over --batch-n seeded spin-boson instances (3 warm-up runs, then
+    --reps timed runs).  Used for ncu captures of the batched kernel on a small case."""
+    import torch
+    from paper_1205_6872_gb300 import quapi as q
+    from paper_1205_6872_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    probs = wl.batched_256(n=args.batch_n, N=args.batch_steps)
+    ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                          q.quapi_opts_init(precision=q.QUAPI_FP32)) for p in probs]
+    try:
+        rho0s, Ns = [p.rho0 for p in probs], [p.N for p in probs]
+        for _ in range(3):
+            q.quapi_propagate_batch(ctxs, rho0s, Ns)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.reps):
+            q.quapi_propagate_batch(ctxs, rho0s, Ns)
+        ms = 1000.0 * (time.perf_counter() - t0) / args.reps
+    finally:
+        for c in ctxs:
+            q.quapi_destroy(c)
+    print(json.dumps(dict(mode="batched-only", instances=len(probs), N=args.batch_steps, ms_per_batch=ms,
+                          value=batch_updates(probs) / (ms / 1e3), unit=UNIT)))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 and DF64 form measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--kernel-only", action="store_true",
@@ -372,11 +399,17 @@ def main():
     ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
     ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"], help="form for --kernel-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="time only the batched launch on a seeded batch (profiling case)")
+    ap.add_argument("--batch-n", type=int, default=256, help="instances for --batched-only")
+    ap.add_argument("--batch-steps", type=int, default=200, help="final step per instance for --batched-only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.batched_only:
+        return run_batched_only(args)
 
     import torch
     world, rank, local = dist_setup()
@@ -401,6 +434,15 @@ def main():
                                                                     for z in r64["rho"].reshape(-1)])
         forms["fp64"]["fp32_vs_fp64_max_abs"] = float(np.abs(r32["rho"] - r64["rho"]).max())
         forms["fp64"]["speedup_fp32_over_fp64"] = r64["ms"] / r32["ms"]
+        forms["fp64"]["roofline"] = dict(bound="alu", unit="GB/s",
+                                         achieved=32.0 * (p.M * p.M) ** p.L / (r64["kernel_ms"] / 1e3) / 1e9,
+                                         note="FP64 pipe saturated (DFMA 1.2 TFLOP/s on this part)")
+        rdf = time_form(q, torch, p, q.QUAPI_DF64, args.steps, args.warmup, stream, world)
+        forms["df64"] = dict(value=world * ups / (rdf["ms"] / 1000.0), unit=UNIT, ms_per_step=rdf["ms"],
+                             kernel_ms=rdf["kernel_ms"],
+                             kernel_GBps=32.0 * (p.M * p.M) ** p.L / (rdf["kernel_ms"] / 1e3) / 1e9,
+                             df64_vs_fp64_max_abs=float(np.abs(rdf["rho"] - r64["rho"]).max()),
+                             speedup_df64_over_fp64=r64["ms"] / rdf["ms"])
     if not args.no_batched:
         forms["batched_256_fp32"] = time_batched(q, torch, args.steps, args.warmup, world, rank)
     e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1))

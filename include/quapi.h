@@ -150,6 +150,24 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
 quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const int64_t* steps,
                                     int nsteps, void* rho_out_dev);
 
+/* Checkpoint and resume.  After quapi_propagate(_device) to a final step N
+ * the context keeps its newest tensor A_{N-1}, which holds everything the
+ * recurrence needs to continue (Sec. I: the tensor propagator is Markovian in
+ * the augmented tensor); quapi_propagate_resume continues from it.
+ *   quapi_get_state: *n = the path point of the kept tensor; with host_buf
+ *     NULL only *bytes is set to its size ((M^2)^min(n+1,L) entries in the
+ *     context's storage format); otherwise *bytes (in: capacity) >= that size
+ *     and the tensor is copied to host_buf (synchronous).
+ *   quapi_set_state: load A_n from host_buf (bytes must equal that size) into
+ *     a context set up with the same inputs; it becomes the kept tensor.
+ *   quapi_propagate_resume: rho at the requested steps, all > n (ascending),
+ *     continuing from the kept tensor; blocks until rho_out is written.
+ * Errors: QUAPI_ERR_ARG (no state yet, size mismatch, steps not after n),
+ * QUAPI_ERR_CUDA. */
+quapi_status quapi_get_state(const quapi_ctx* c, int64_t* n, void* host_buf, size_t* bytes);
+quapi_status quapi_set_state(quapi_ctx* c, int64_t n, const void* host_buf, size_t bytes);
+quapi_status quapi_propagate_resume(quapi_ctx* c, const int64_t* steps, int nsteps, double* rho_out);
+
 /* One tensor-propagator step on caller device buffers: the step that adds
  * path point n (n >= 1) to A_{n-1} (Sec. I, multiply by the propagator tensor
  * T and, once A_{n-1} holds L points, sum over the oldest index).

@@ -263,12 +263,16 @@ template <int M, int FORM> struct StepTables {
 };
 
 // All outputs (and readout contributions) of the FPT fibers f0.. held in registers.
-template <int M, int FORM, bool WRITE, bool READ, bool DIAG>
+// hpre / hepre: the hi entries of this thread's fibers staged by the caller
+// (row x at hpre[x * HSTRIDE]; all FPT fibers share one f_hi), or null to load them here.
+template <int M, int FORM, bool WRITE, bool READ, bool DIAG, int HSTRIDE = 1>
 __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
                                                typename FormT<FORM>::Elem (&a)[FormT<FORM>::FPT][M * M],
                                                const bool (&valid)[FormT<FORM>::FPT], int64_t f0, int64_t F,
                                                typename FormT<FORM>::Elem* __restrict__ out,
-                                               RhoAcc<FORM> (&racc)[M * M]) {
+                                               RhoAcc<FORM> (&racc)[M * M],
+                                               const typename FormT<FORM>::Tab* hpre = nullptr,
+                                               const typename FormT<FORM>::Tab* hepre = nullptr) {
     constexpr int M2 = M * M;
     using Elem = typename FormT<FORM>::Elem;
     constexpr int FPT = FormT<FORM>::FPT;
@@ -290,8 +294,8 @@ __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
         Elem vread[FPT];
         const bool diag_row = DIAG && is_diag<M>(x);
         typename FormT<FORM>::Tab h0, he0;
-        if (WRITE) h0 = T.hi[(int64_t)x * T.hi_size + fhi[0]];
-        if (READ && !(WRITE && diag_row)) he0 = T.hie[(int64_t)x * T.hi_size + fhi[0]];
+        if (WRITE) h0 = hpre ? hpre[x * HSTRIDE] : T.hi[(int64_t)x * T.hi_size + fhi[0]];
+        if (READ && !(WRITE && diag_row)) he0 = hepre ? hepre[x * HSTRIDE] : T.hie[(int64_t)x * T.hi_size + fhi[0]];
 #pragma unroll
         for (int u = 0; u < FPT; ++u) {
             if (!valid[u]) {
@@ -439,6 +443,12 @@ __device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap* m
         : "memory");
 }
 
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 template <int M, int FORM, bool WRITE, bool READ, bool DIAG, int STAGES>
 __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constant__ CUtensorMap in_map,
                                                             StepArgs args) {
@@ -453,8 +463,15 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
     static_assert(STAGES * 8 <= kBarBytes, "mbarriers fit their slot");
+    using Tab = typename FormT<FORM>::Tab;
+    // hi entries of one tile: TILE / lo_size (= HPT) consecutive f_hi per row, copied with the tile.
+    // They are read after the stage is released, so their ring has one slot more than the tile
+    // ring: the refill issued in iteration k overwrites the slot of tile k - 1, never that of tile k.
+    constexpr int HPT = TILE / 256;
+    constexpr int HSLOTS = STAGES + 1;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + STAGES * kTmaTileBytes);
-    unsigned char* tables = ring + STAGES * kTmaTileBytes + kBarBytes;  // 16-byte aligned
+    Tab* hring = reinterpret_cast<Tab*>(ring + STAGES * kTmaTileBytes + kBarBytes);  // [HSLOTS][2][M2][HPT]
+    unsigned char* tables = reinterpret_cast<unsigned char*>(hring + HSLOTS * 2 * M2 * HPT);
 
     StepTables<M, FORM> T;
     T.template stage<WRITE, READ>(args, tables);
@@ -463,6 +480,23 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     const int64_t ntiles = F / TILE;
     const int64_t my_tiles = (blockIdx.x < ntiles) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     uint64_t policy = 0;
+    const Tab* ghi = reinterpret_cast<const Tab*>(args.hi);
+    const Tab* ghie = reinterpret_cast<const Tab*>(args.hi_e);
+    const int64_t hi_size = F >> T.lo_shift;
+    // one tile: the 16 KB TMA box plus, per row, its HPT hi entries (and the readout's)
+    auto issue_tile = [&](int st, int hs, int64_t tile) {
+        constexpr uint32_t hb = HPT * sizeof(Tab);
+        const uint32_t bytes = kTmaTileBytes + (WRITE ? M2 * hb : 0) + (READ ? M2 * hb : 0);
+        const uint32_t bar = smem_u32(&bars[st]);
+        mbar_expect_tx(bar, bytes);
+        tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows), bar, policy);
+        const int64_t fh0 = tile * HPT;
+#pragma unroll
+        for (int x = 0; x < M2; ++x) {
+            if (WRITE) bulk_load(smem_u32(hring + ((hs * 2 + 0) * M2 + x) * HPT), ghi + x * hi_size + fh0, hb, bar);
+            if (READ) bulk_load(smem_u32(hring + ((hs * 2 + 1) * M2 + x) * HPT), ghie + x * hi_size + fh0, hb, bar);
+        }
+    };
     if (threadIdx.x == 0) {
         asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
         for (int st = 0; st < STAGES; ++st) mbar_init(smem_u32(&bars[st]), 1);
@@ -473,9 +507,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES && st < my_tiles; ++st) {
             const int64_t tile = blockIdx.x + (int64_t)st * gridDim.x;
-            mbar_expect_tx(smem_u32(&bars[st]), kTmaTileBytes);
-            tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows),
-                          smem_u32(&bars[st]), policy);
+            issue_tile(st, st % HSLOTS, tile);
         }
     }
 
@@ -489,7 +521,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     for (int64_t k = 0; k < my_tiles; ++k) {
         const int st = (int)(k % STAGES);
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
+        const int64_t f0 = (blockIdx.x + k * gridDim.x) * TILE + (int64_t)threadIdx.x * FPT;
         const bool ok = mbar_wait_bounded(smem_u32(&bars[st]), parity, kWaitLimitNs);
+        // this thread's FPT fibers share one f_hi (lo_size = 256 on this path): entry (threadIdx.x * FPT) / 256
+        const int hsel = (int)(((int64_t)threadIdx.x * FPT) >> 8);
+        const int hs = (int)(k % HSLOTS);
+        const Tab* hv = hring + (hs * 2 + 0) * M2 * HPT + hsel;
+        const Tab* hve = hring + (hs * 2 + 1) * M2 * HPT + hsel;
         Elem a[FPT][M2];
         if (ok) {
             const unsigned char* row = ring + st * kTmaTileBytes + r * 128;
@@ -520,15 +558,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
         if (threadIdx.x == 0 && k + STAGES < my_tiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads of the stage before the copy
             const int64_t tile = blockIdx.x + (k + STAGES) * gridDim.x;
-            mbar_expect_tx(smem_u32(&bars[st]), kTmaTileBytes);
-            tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows),
-                          smem_u32(&bars[st]), policy);
+            issue_tile(st, (int)((k + STAGES) % HSLOTS), tile);
         }
-        const int64_t f0 = (blockIdx.x + k * gridDim.x) * TILE + (int64_t)threadIdx.x * FPT;
         bool valid[FPT];
 #pragma unroll
         for (int u = 0; u < FPT; ++u) valid[u] = true;
-        process_fibers<M, FORM, WRITE, READ, DIAG>(T, a, valid, f0, F, out, racc);
+        process_fibers<M, FORM, WRITE, READ, DIAG, HPT>(T, a, valid, f0, F, out, racc, WRITE ? hv : nullptr,
+                                                        READ ? hve : nullptr);
     }
     if (READ) write_partials<M2, FORM>(racc, args.partial);
 }
@@ -627,7 +663,10 @@ bool encode_rows_map(CUtensorMap* map, const void* base, int64_t bytes) {
 
 template <int FORM, bool W, bool R, bool D, int STAGES>
 cudaError_t launch_tma_variant(StepArgs& a, const CUtensorMap& map, cudaStream_t st) {
-    size_t smem = 1024 + (size_t)STAGES * kTmaTileBytes + kBarBytes + StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+    constexpr int HPT = (kThreads * FormT<FORM>::FPT) / 256;
+    size_t smem = 1024 + (size_t)STAGES * kTmaTileBytes + kBarBytes +
+                  (size_t)(STAGES + 1) * 2 * 4 * HPT * sizeof(typename FormT<FORM>::Tab) +
+                  StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = step_kernel_tma<2, FORM, W, R, D, STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -660,7 +699,7 @@ cudaError_t launch_tma_stages(StepArgs& a, const CUtensorMap& map, cudaStream_t 
 template <int M, int FORM>
 cudaError_t launch_step_mf(StepArgs& a, cudaStream_t st) {
     const bool W = a.A_out != nullptr, R = a.partial != nullptr;
-    if constexpr (M == 2) if (a.use_tma && a.diag_fast) {
+    if constexpr (M == 2) if (a.use_tma && a.diag_fast && a.lo_size == 256) {
         constexpr int FPT = FormT<FORM>::FPT;
         const int64_t elt = (FORM == QUAPI_FP32) ? 8 : 16;
         CUtensorMap map;

@@ -74,6 +74,8 @@ struct quapi_ctx {
     bool use_tma = true;         // M = 2: TMA-staged step kernel when the tensor allows it
     int stages = 2;              // its ring depth (2 measured best: 4 CTAs per SM fit)
     bool tune = false;           // quapi_opts.tune
+    int64_t state_n = -1;        // path point of the newest tensor kept in buf[state_buf] (-1: none)
+    int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
@@ -471,6 +473,33 @@ quapi_status check_device_error(quapi_ctx* c) {
 }
 
 // Enqueue the whole propagation; rho(t_steps[i]) lands in slots[i] (device).
+// Steps n = n_from + 1 .. N starting from A_{n_from} in buf[cur]; rho at the
+// requested steps (those > n_from) lands in slots.  The newest tensor computed,
+// A_{N-1}, stays in the context as its state.
+quapi_status run_steps(quapi_ctx* c, int64_t n_from, int cur, const int64_t* steps, int nsteps, int next,
+                       double2* slots) {
+    const int64_t N = steps[nsteps - 1];
+    c->state_n = n_from;
+    c->state_buf = cur;
+    for (int64_t n = n_from + 1; n <= N; ++n) {
+        double2* slot = nullptr;
+        if (next < nsteps && steps[next] == n) {
+            slot = slots + (size_t)next * c->M2;
+            ++next;
+        }
+        void* A_out = (n < N) ? c->buf[cur ^ 1] : nullptr;
+        quapi_status s = run_point(c, n, c->buf[cur], A_out, slot);
+        if (s != QUAPI_OK) return s;
+        if (A_out) {
+            cur ^= 1;
+            c->state_n = n;
+            c->state_buf = cur;
+        }
+    }
+    return QUAPI_OK;
+}
+
+// Enqueue the whole propagation; rho(t_steps[i]) lands in slots[i] (device).
 quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int64_t* steps, int nsteps,
                                double2* slots) {
     const int64_t N = steps[nsteps - 1];
@@ -480,20 +509,22 @@ quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int6
                "copy rho0");
         next = 1;
     }
+    c->state_n = -1;
     if (N == 0) return QUAPI_OK;
-    int cur = 0;
-    QCHECK(c, launch_init_tensor(rho0_dev, c->d_eta, eta_self0(c->L), c->d_s, c->M, c->form, c->buf[cur], c->st),
+    QCHECK(c, launch_init_tensor(rho0_dev, c->d_eta, eta_self0(c->L), c->d_s, c->M, c->form, c->buf[0], c->st),
            "init tensor kernel");
-    for (int64_t n = 1; n <= N; ++n) {
-        double2* slot = nullptr;
-        if (next < nsteps && steps[next] == n) {
-            slot = slots + (size_t)next * c->M2;
-            ++next;
-        }
-        void* A_out = (n < N) ? c->buf[cur ^ 1] : nullptr;
-        quapi_status s = run_point(c, n, c->buf[cur], A_out, slot);
-        if (s != QUAPI_OK) return s;
-        if (A_out) cur ^= 1;
+    return run_steps(c, 0, 0, steps, nsteps, next, slots);
+}
+
+int64_t state_elements(const quapi_ctx* c, int64_t n) { return ipow(c->M2, (int)std::min<int64_t>(n + 1, c->L)); }
+
+quapi_status ensure_slots(quapi_ctx* c, int nsteps) {
+    if (c->slots_cap < (size_t)nsteps) {
+        if (c->d_slots) cudaFree(c->d_slots);
+        c->d_slots = nullptr;
+        c->slots_cap = 0;
+        QCHECK(c, cudaMalloc(&c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps), "cudaMalloc(rho slots)");
+        c->slots_cap = nsteps;
     }
     return QUAPI_OK;
 }
@@ -625,13 +656,8 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
     if (!rho0 || !rho_out) return fail(c, QUAPI_ERR_ARG, "rho0 and rho_out must not be NULL");
     quapi_status s = check_steps(c, steps, nsteps);
     if (s != QUAPI_OK) return s;
-    if (c->slots_cap < (size_t)nsteps) {
-        if (c->d_slots) cudaFree(c->d_slots);
-        c->d_slots = nullptr;
-        c->slots_cap = 0;
-        QCHECK(c, cudaMalloc(&c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps), "cudaMalloc(rho slots)");
-        c->slots_cap = nsteps;
-    }
+    s = ensure_slots(c, nsteps);
+    if (s != QUAPI_OK) return s;
     QCHECK(c, cudaMemcpyAsync(c->d_rho0, rho0, sizeof(double2) * c->M2, cudaMemcpyHostToDevice, c->st), "copy rho0");
     s = propagate_enqueue(c, c->d_rho0, steps, nsteps, c->d_slots);
     if (s != QUAPI_OK) return s;
@@ -639,6 +665,52 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
                               c->st),
            "copy rho");
     QCHECK(c, cudaStreamSynchronize(c->st), "propagate synchronize");
+    return check_device_error(c);
+}
+
+quapi_status quapi_get_state(const quapi_ctx* c, int64_t* n, void* host_buf, size_t* bytes) {
+    quapi_ctx* m = const_cast<quapi_ctx*>(c);
+    if (!c || !n || !bytes) return fail(m, QUAPI_ERR_ARG, "NULL argument");
+    if (c->state_n < 0) return fail(m, QUAPI_ERR_ARG, "no propagation state yet (propagate to a step >= 2 first)");
+    const size_t need = (size_t)state_elements(c, c->state_n) * elem_bytes(c->form);
+    *n = c->state_n;
+    if (!host_buf) {
+        *bytes = need;
+        return QUAPI_OK;
+    }
+    if (*bytes < need) return fail(m, QUAPI_ERR_ARG, "state buffer too small");
+    *bytes = need;
+    QCHECK(m, cudaMemcpyAsync(host_buf, c->buf[c->state_buf], need, cudaMemcpyDeviceToHost, c->st), "copy state");
+    QCHECK(m, cudaStreamSynchronize(c->st), "synchronize");
+    return QUAPI_OK;
+}
+
+quapi_status quapi_set_state(quapi_ctx* c, int64_t n, const void* host_buf, size_t bytes) {
+    if (!c || !host_buf) return fail(c, QUAPI_ERR_ARG, "NULL argument");
+    if (n < 0) return fail(c, QUAPI_ERR_ARG, "n must be >= 0");
+    const size_t need = (size_t)state_elements(c, n) * elem_bytes(c->form);
+    if (bytes != need) return fail(c, QUAPI_ERR_ARG, "state size does not match (M^2)^min(n+1,L) entries");
+    QCHECK(c, cudaMemcpyAsync(c->buf[0], host_buf, need, cudaMemcpyHostToDevice, c->st), "copy state");
+    c->state_n = n;
+    c->state_buf = 0;
+    return QUAPI_OK;
+}
+
+quapi_status quapi_propagate_resume(quapi_ctx* c, const int64_t* steps, int nsteps, double* rho_out) {
+    if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
+    if (!rho_out) return fail(c, QUAPI_ERR_ARG, "rho_out must not be NULL");
+    quapi_status s = check_steps(c, steps, nsteps);
+    if (s != QUAPI_OK) return s;
+    if (c->state_n < 0) return fail(c, QUAPI_ERR_ARG, "no state to resume from");
+    if (steps[0] <= c->state_n) return fail(c, QUAPI_ERR_ARG, "resume steps must lie after the state's step");
+    s = ensure_slots(c, nsteps);
+    if (s != QUAPI_OK) return s;
+    s = run_steps(c, c->state_n, c->state_buf, steps, nsteps, 0, c->d_slots);
+    if (s != QUAPI_OK) return s;
+    QCHECK(c, cudaMemcpyAsync(rho_out, c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps, cudaMemcpyDeviceToHost,
+                              c->st),
+           "copy rho");
+    QCHECK(c, cudaStreamSynchronize(c->st), "resume synchronize");
     return check_device_error(c);
 }
 

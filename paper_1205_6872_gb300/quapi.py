@@ -40,7 +40,8 @@ JKIND = {"ohmic_exp": QUAPI_J_OHMIC_EXP, "superohmic_gauss": QUAPI_J_SUPEROHMIC_
 EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_setup", "quapi_setup_eta",
             "quapi_propagate", "quapi_propagate_device", "quapi_step_device",
             "quapi_propagate_batch", "quapi_get_eta", "quapi_get_propagator",
-            "quapi_readout_static", "quapi_kernel_launches", "quapi_last_error", "quapi_destroy")
+            "quapi_readout_static", "quapi_get_state", "quapi_set_state", "quapi_propagate_resume",
+            "quapi_kernel_launches", "quapi_last_error", "quapi_destroy")
 
 
 class quapi_spectral(ctypes.Structure):
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
             "quapi_get_eta": (ctypes.c_int, [ctxp, dp]),
             "quapi_get_propagator": (ctypes.c_int, [ctxp, dp, dp]),
             "quapi_readout_static": (ctypes.c_int, [ctxp, ctypes.c_int64, vp, vp]),
+            "quapi_get_state": (ctypes.c_int, [ctxp, i64p, vp, ctypes.POINTER(ctypes.c_size_t)]),
+            "quapi_set_state": (ctypes.c_int, [ctxp, ctypes.c_int64, vp, ctypes.c_size_t]),
+            "quapi_propagate_resume": (ctypes.c_int, [ctxp, i64p, ctypes.c_int, dp]),
             "quapi_kernel_launches": (ctypes.c_uint64, []),
             "quapi_last_error": (ctypes.c_char_p, [ctxp]),
             "quapi_destroy": (None, [ctxp]),
@@ -232,6 +236,29 @@ def quapi_get_propagator(ctx, M):
 def quapi_readout_static(ctx, n, A_in_dev, rho_dev):
     """rho(t_n) from A_{n-1} into rho_dev, with the readout scratch in the library's fixed array."""
     _check(load().quapi_readout_static(ctx, int(n), _dev_ptr(A_in_dev), _dev_ptr(rho_dev)), ctx)
+
+
+def quapi_get_state(ctx):
+    """(n, bytes) of the context's kept tensor A_n, copied to host as a uint8 numpy array."""
+    n = ctypes.c_int64()
+    nb = ctypes.c_size_t(0)
+    _check(load().quapi_get_state(ctx, ctypes.byref(n), None, ctypes.byref(nb)), ctx)
+    buf = np.empty(nb.value, dtype=np.uint8)
+    _check(load().quapi_get_state(ctx, ctypes.byref(n), buf.ctypes.data, ctypes.byref(nb)), ctx)
+    return n.value, buf
+
+
+def quapi_set_state(ctx, n, state):
+    buf = np.ascontiguousarray(state).view(np.uint8)
+    _check(load().quapi_set_state(ctx, int(n), buf.ctypes.data, buf.nbytes), ctx)
+
+
+def quapi_propagate_resume(ctx, steps, M):
+    st = np.ascontiguousarray(np.asarray(steps, dtype=np.int64))
+    out = np.empty(st.size * M * M, dtype=np.complex128)
+    _check(load().quapi_propagate_resume(ctx, st.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), st.size,
+                                         _dp(out.view(np.float64))), ctx)
+    return out.reshape(st.size, M, M)
 
 
 def quapi_kernel_launches() -> int:

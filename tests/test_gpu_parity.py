@@ -257,3 +257,35 @@ def test_argument_errors(q):
         assert e.value.status == q.QUAPI_ERR_ARG
     finally:
         q.quapi_destroy(ctx)
+
+
+# ---------------------------------------------------------------- checkpoint / resume
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5), (48, 1e-12)])
+def test_checkpoint_resume_matches_uninterrupted(q, prec, tol):
+    p = wl.spin_boson_L6()
+    full_steps = [10, 25, 40, 60]
+    want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, full_steps)
+    c1 = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(precision=prec))
+    c2 = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(precision=prec))
+    try:
+        first = q.quapi_propagate(c1, p.rho0, [10, 25], p.M)
+        n, state = q.quapi_get_state(c1)
+        assert n == 24
+        # a fresh context with the same inputs continues from the saved tensor
+        q.quapi_set_state(c2, n, state)
+        rest = q.quapi_propagate_resume(c2, [40, 60], p.M)
+        # and the original context can continue too
+        rest1 = q.quapi_propagate_resume(c1, [40, 60], p.M)
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate_resume(c1, [30], p.M)   # not after the kept tensor (now A_59)
+        assert e.value.status == q.QUAPI_ERR_ARG
+        with pytest.raises(q.QuapiError):
+            q.quapi_set_state(c2, 3, state)            # size does not match A_3
+    finally:
+        q.quapi_destroy(c1)
+        q.quapi_destroy(c2)
+    for got, k in zip(list(first) + list(rest), full_steps):
+        assert np.abs(got - want[k]).max() <= tol, k
+    for got, k in zip(rest1, [40, 60]):
+        assert np.abs(got - want[k]).max() <= tol, k
