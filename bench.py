@@ -330,11 +330,14 @@ def run_kernel_only(args):
     L = args.dkmax
     prec = {"fp32": q.QUAPI_FP32, "fp64": q.QUAPI_FP64, "df64": q.QUAPI_DF64}[args.form]
     tbytes, _ = q.quapi_query_memory(p.M, L, prec)
+    if args.hermitian:
+        from paper_1205_6872_gb300 import layout
+        tbytes = 2 * layout.count(L) * (8 if prec == q.QUAPI_FP32 else 16)
     ws = torch.empty(tbytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
     ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, L,
                         q.quapi_opts_init(precision=prec, cuda_stream=stream, workspace=ws,
-                                          workspace_bytes=tbytes))
+                                          workspace_bytes=tbytes, hermitian=int(args.hermitian)))
     try:
         half = tbytes // 2
         A, B = ws.data_ptr(), ws.data_ptr() + half
@@ -354,7 +357,8 @@ def run_kernel_only(args):
     finally:
         q.quapi_destroy(ctx)
     gbs = tbytes / (ms / 1000.0) / 1e9
-    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, kernel_ms=ms, GBps=gbs)))
+    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, hermitian=bool(args.hermitian), kernel_ms=ms,
+                          GBps=gbs, logical_updates_per_s=float((p.M * p.M) ** L) / (ms / 1000.0))))
     return 0
 
 
@@ -399,6 +403,7 @@ def main():
     ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
     ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"], help="form for --kernel-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
+    ap.add_argument("--hermitian", action="store_true", help="--kernel-only: Hermitian half layout")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the batched launch on a seeded batch (profiling case)")
     ap.add_argument("--batch-n", type=int, default=256, help="instances for --batched-only")

@@ -688,6 +688,8 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
+        if (ctx_half_layout(ctxs[i]))
+            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: contexts in the Hermitian half layout run alone");
         if (form == QUAPI_DF64)
             return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: the double-float form runs one context at a time");
         uids[i] = ctx_uid(ctxs[i]);

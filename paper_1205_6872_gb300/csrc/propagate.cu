@@ -569,6 +569,224 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     if (READ) write_partials<M2, FORM>(racc, args.partial);
 }
 
+// ---- Hermitian half layout (M = 2) ------------------------------------------------
+//
+// For a Hermitian rho(0), A(conj path) = conj(A(path)) (swapping s+ and s- of
+// every point conjugates K and every influence factor).  Only canonical entries
+// are stored: an index is canonical when its most significant digit outside
+// {0, 3} is a 1.  Layout of n digits: [top 1: 4^(n-1) plain continuations]
+// [top 0: half layout of n-1 digits] [top 3: half layout of n-1 digits],
+// C(n) = (4^n + 2^n)/2 entries; every last-digit fiber stays contiguous
+// (4 entries, or 3 stored as 1, 0, 3 for a prefix of only 0s and 3s).
+// One thread per canonical prefix f computes the rows the half layout keeps:
+// (1, f), (1, conj f) from the same loaded fiber, and (0, f), (3, f); the
+// readout adds row 1 over f and conj f and twice the real part of the
+// diagonal rows (their conjugate partners are conjugates).
+
+__host__ __device__ __forceinline__ int64_t half_count(int n) {
+    return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1;
+}
+
+// canonical position c of an n-digit half layout -> plain index, number of
+// self-conjugate entries before c, and whether c is self-conjugate
+__device__ __forceinline__ void half_decode(int64_t c, int n, uint32_t& plain, int64_t& sc_before, bool& sc) {
+    uint32_t p = 0;
+    int64_t s = 0;
+    for (int level = n; level >= 1; --level) {
+        const int64_t r1 = int64_t(1) << (2 * (level - 1));
+        if (c < r1) {  // digit 1, the rest is plain
+            plain = (p << (2 * level)) | (uint32_t(1) << (2 * (level - 1))) | (uint32_t)c;
+            sc_before = s;
+            sc = false;
+            return;
+        }
+        c -= r1;
+        const int64_t cn1 = half_count(level - 1);
+        if (c < cn1) {
+            p = (p << 2) | 0u;
+        } else {
+            c -= cn1;
+            s += int64_t(1) << (level - 1);
+            p = (p << 2) | 3u;
+        }
+    }
+    plain = p;
+    sc_before = s;
+    sc = true;
+}
+
+__device__ __forceinline__ uint32_t conj_digits(uint32_t f) {
+    return ((f & 0x55555555u) << 1) | ((f & 0xAAAAAAAAu) >> 1);
+}
+
+__device__ __forceinline__ double2 conjv(double2 v) { return make_double2(v.x, -v.y); }
+__device__ __forceinline__ float2 conjv(float2 v) { return make_float2(v.x, -v.y); }
+__device__ __forceinline__ df2 conjv(df2 v) {
+    v.h.y = -v.h.y;
+    v.l.y = -v.l.y;
+    return v;
+}
+__device__ __forceinline__ double2 twice_real(double2 v) { return make_double2(2.0 * v.x, 0.0); }
+__device__ __forceinline__ float2 twice_real(float2 v) { return make_float2(2.f * v.x, 0.f); }
+__device__ __forceinline__ df2 twice_real(df2 v) {
+    v.h = make_float2(2.f * v.h.x, 0.f);
+    v.l = make_float2(2.f * v.l.x, 0.f);
+    return v;
+}
+__device__ __forceinline__ double2 real_part(double2 v) { return make_double2(v.x, 0.0); }
+__device__ __forceinline__ float2 real_part(float2 v) { return make_float2(v.x, 0.f); }
+__device__ __forceinline__ df2 real_part(df2 v) {
+    v.h.y = 0.f;
+    v.l.y = 0.f;
+    return v;
+}
+__device__ __forceinline__ double2 ld_plain(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_plain(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ df2 ld_plain(const df2* p) { return ld_stream(p); }
+
+// outputs of rows 0, 1, 3 for one fiber a (row 2 is never stored)
+template <int FORM, bool DIAG, bool END>
+__device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const typename FormT<FORM>::Elem (&a)[4],
+                                          uint32_t f, typename FormT<FORM>::Elem (&o)[4]) {
+    using Tab = typename FormT<FORM>::Tab;
+    const uint32_t fh = f >> T.lo_shift, fl = f & (T.lo_size - 1u);
+    const Tab* isum = END ? T.isume : T.isum;
+    const Tab* lo = END ? T.loe : T.lo;
+    const Tab* hi = END ? T.hie : T.hi;
+    if (DIAG) {
+        const auto S = plain_sum<4>(a);
+        o[0] = apply_hi(hi[fh], S);
+        o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
+    } else {
+        o[0] = apply_p(hi[fh], lo[fl], row_sum<4>(isum, a));
+        o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4>(isum + 12, a));
+    }
+    o[1] = apply_p(hi[T.hi_size + fh], lo[T.lo_size + fl], row_sum<4>(isum + 4, a));
+}
+
+template <int FORM, bool WRITE, bool READ, bool DIAG>
+__global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
+    using Elem = typename FormT<FORM>::Elem;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepTables<2, FORM> T;
+    T.template stage<WRITE, READ>(args, smem_raw);
+    __syncthreads();
+    RhoAcc<FORM> racc[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) racc[x].init();
+    const Elem* __restrict__ A = reinterpret_cast<const Elem*>(args.A_in);
+    Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
+    const int npre_digits = args.half_digits;  // digits of the prefix f (n_in - 1)
+    const int64_t npre = half_count(npre_digits);
+    const int64_t F = args.F;                  // 4^(n_in - 1): size of the plain row-1 block
+    constexpr int remap[4] = {0, 2, 1, 3};
+    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < npre; c += (int64_t)gridDim.x * kThreads) {
+        uint32_t f;
+        int64_t s;
+        bool sc;
+        half_decode(c, npre_digits, f, s, sc);
+        const int64_t pin = 4 * c - s;
+        Elem a[4], b[4];
+        if (!sc) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = ld_plain(A + pin + q);
+        } else {  // stored as old = 1, 0, 3; old = 2 is the conjugate of old = 1
+            a[1] = ld_plain(A + pin);
+            a[0] = ld_plain(A + pin + 1);
+            a[3] = ld_plain(A + pin + 2);
+            a[2] = conjv(a[1]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = conjv(a[remap[q]]);  // fiber of the conjugate prefix
+        const uint32_t fb = conj_digits(f);
+        if (WRITE) {
+            Elem o[4];
+            herm_rows<FORM, DIAG, false>(T, a, f, o);
+            st_stream(out + f, o[1]);
+            st_stream(out + F + c, o[0]);
+            st_stream(out + F + npre + c, o[3]);
+            if (!sc) {
+                Elem ob[4];
+                herm_rows<FORM, DIAG, false>(T, b, fb, ob);
+                st_stream(out + fb, ob[1]);
+            }
+        }
+        if (READ) {
+            Elem r[4];
+            herm_rows<FORM, DIAG, true>(T, a, f, r);
+            racc[1].add(r[1]);
+            if (!sc) {
+                Elem rb[4];
+                herm_rows<FORM, DIAG, true>(T, b, fb, rb);
+                racc[1].add(rb[1]);
+                racc[0].add(twice_real(r[0]));
+                racc[3].add(twice_real(r[3]));
+            } else {
+                racc[0].add(real_part(r[0]));
+                racc[3].add(real_part(r[3]));
+            }
+        }
+    }
+    if (READ) {
+        // row 2 of rho is the conjugate of row 1
+        __shared__ double2 red[kThreads / 32][4];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            if (x == 2) continue;
+            double2 v = racc[x].value();
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+                v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+            }
+            if (lane == 0) red[warp][x] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && threadIdx.x != 2) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int w = 0; w < kThreads / 32; ++w) v = cadd(v, red[w][threadIdx.x]);
+            args.partial[(int64_t)blockIdx.x * 4 + threadIdx.x] = v;
+            if (threadIdx.x == 1) args.partial[(int64_t)blockIdx.x * 4 + 2] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+// growth in the half layout: input n_in digits (C(n_in) entries) -> n_in + 1 digits
+template <int FORM>
+__global__ void __launch_bounds__(kThreads) herm_grow_kernel(const void* __restrict__ A_in_, void* __restrict__ A_out_,
+                                                             int n_in, const void* __restrict__ lo_,
+                                                             const void* __restrict__ hi_, int64_t lo_size_,
+                                                             int lo_shift) {
+    using Elem = typename FormT<FORM>::Elem;
+    using Tab = typename FormT<FORM>::Tab;
+    const Elem* A = reinterpret_cast<const Elem*>(A_in_);
+    Elem* out = reinterpret_cast<Elem*>(A_out_);
+    const Tab* lo = reinterpret_cast<const Tab*>(lo_);
+    const Tab* hi = reinterpret_cast<const Tab*>(hi_);
+    const int64_t S = int64_t(1) << (2 * n_in);
+    const int64_t Cn = half_count(n_in);
+    const uint32_t lo_size = (uint32_t)lo_size_;
+    const int64_t hi_size = S / lo_size_;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Cn; c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i;
+        int64_t s;
+        bool sc;
+        half_decode(c, n_in, i, s, sc);
+        const Elem v = A[c];
+        auto P = [&](int x, uint32_t idx, Elem w) {
+            return tmul(hi[(int64_t)x * hi_size + (idx >> lo_shift)], tmul(lo[(int64_t)x * lo_size + (idx & (lo_size - 1u))], w));
+        };
+        out[i] = P(1, i, v);
+        if (!sc) {
+            const uint32_t ib = conj_digits(i);
+            out[ib] = P(1, ib, conjv(v));
+        }
+        out[S + c] = P(0, i, v);
+        out[S + Cn + c] = P(3, i, v);
+    }
+}
+
 template <int M, int FORM>
 __global__ void __launch_bounds__(kThreads) grow_kernel(const void* __restrict__ A_in_, void* __restrict__ A_out_,
                                                         int64_t S, const void* __restrict__ lo_,
@@ -742,6 +960,69 @@ cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st) {
     if (M == 2 && form == QUAPI_DF64) return launch_step_mf<2, QUAPI_DF64>(a, st);
     if (M == 3 && form == QUAPI_DF64) return launch_step_mf<3, QUAPI_DF64>(a, st);
     return cudaErrorInvalidValue;
+}
+
+namespace {
+template <int FORM, bool W, bool R, bool D>
+cudaError_t launch_herm_variant(StepArgs& a, cudaStream_t st) {
+    size_t smem = StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+    auto kern = herm_step_kernel<FORM, W, R, D>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t work = (half_count(a.half_digits) + kThreads - 1) / kThreads;
+    int64_t g = (int64_t)num_sms() * (occ < 1 ? 1 : occ);
+    if (g > work) g = work;
+    if (g > a.grid) g = a.grid;
+    if (g < 1) g = 1;
+    a.grid = (int)g;
+    kern<<<a.grid, kThreads, smem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+template <int FORM>
+cudaError_t launch_herm_form(StepArgs& a, cudaStream_t st) {
+    const bool W = a.A_out != nullptr, R = a.partial != nullptr;
+    if (a.diag_fast) {
+        if (W && R) return launch_herm_variant<FORM, true, true, true>(a, st);
+        if (W) return launch_herm_variant<FORM, true, false, true>(a, st);
+        if (R) return launch_herm_variant<FORM, false, true, true>(a, st);
+    } else {
+        if (W && R) return launch_herm_variant<FORM, true, true, false>(a, st);
+        if (W) return launch_herm_variant<FORM, true, false, false>(a, st);
+        if (R) return launch_herm_variant<FORM, false, true, false>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_herm_step(int form, StepArgs& a, cudaStream_t st) {
+    if (form == QUAPI_FP64) return launch_herm_form<QUAPI_FP64>(a, st);
+    if (form == QUAPI_FP32) return launch_herm_form<QUAPI_FP32>(a, st);
+    if (form == QUAPI_DF64) return launch_herm_form<QUAPI_DF64>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
+                             int64_t lo_size, int lo_shift, cudaStream_t st) {
+    const int64_t Cn = half_count(n_in);
+    int64_t blocks = (Cn + kThreads - 1) / kThreads;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+    if (blocks < 1) blocks = 1;
+    if (form == QUAPI_FP64)
+        herm_grow_kernel<QUAPI_FP64><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size, lo_shift);
+    else if (form == QUAPI_FP32)
+        herm_grow_kernel<QUAPI_FP32><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size, lo_shift);
+    else if (form == QUAPI_DF64)
+        herm_grow_kernel<QUAPI_DF64><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size, lo_shift);
+    else
+        return cudaErrorInvalidValue;
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t S, const void* lo,

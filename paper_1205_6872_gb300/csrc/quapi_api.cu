@@ -53,6 +53,7 @@ int64_t ipow(int64_t b, int e) {
 }
 
 int max_dkmax(int M) { return M == 2 ? 16 : 10; }
+int64_t half_entries(int n) { return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1; }
 int lo_digits_max(int M) { return M == 2 ? 4 : 2; }
 
 }  // namespace
@@ -74,6 +75,7 @@ struct quapi_ctx {
     bool use_tma = true;         // M = 2: TMA-staged step kernel when the tensor allows it
     int stages = 2;              // its ring depth (2 measured best: 4 CTAs per SM fit)
     bool tune = false;           // quapi_opts.tune
+    bool herm = false;           // Hermitian half layout (M = 2)
     int64_t state_n = -1;        // path point of the newest tensor kept in buf[state_buf] (-1: none)
     int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
@@ -225,6 +227,7 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
             return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64, QUAPI_FP32 or QUAPI_DF64");
         if (o->endpoint_mode != QUAPI_ENDPOINT_STRANG && o->endpoint_mode != QUAPI_ENDPOINT_INTERIOR)
             return fail(nullptr, QUAPI_ERR_ARG, "unknown endpoint_mode");
+        if (o->hermitian && M != 2) return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "the Hermitian half layout needs M = 2");
     }
     return QUAPI_OK;
 }
@@ -248,7 +251,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, QUAPI_ERR_ARG, "beta must be > 0");
     }
     const int M2 = M * M;
-    const int64_t nelem = ipow(M2, L);
+    const int64_t nelem = o.hermitian ? half_entries(L) : ipow(M2, L);
     const size_t tensor_bytes = 2 * (size_t)nelem * elem_bytes(o.precision);
     if (o.workspace && o.workspace_bytes < tensor_bytes)
         return fail(nullptr, QUAPI_ERR_OOM, "caller workspace smaller than the two tensors");
@@ -263,6 +266,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     c->st = reinterpret_cast<cudaStream_t>(o.cuda_stream);
     c->host_s.assign(s, s + M);
     c->tune = o.tune != 0;
+    c->herm = o.hermitian != 0;
     {
         static std::atomic<uint64_t> next_uid{1};
         c->uid = next_uid.fetch_add(1);
@@ -420,7 +424,11 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
     a.use_tma = c->use_tma;
     a.stages = c->stages;
     a.err_flag = c->d_err;
-    QCHECK(c, launch_step(c->M, c->form, a, c->st), "step kernel");
+    a.half_digits = c->herm ? ref->n_in - 1 : -1;
+    if (c->herm)
+        QCHECK(c, launch_herm_step(c->form, a, c->st), "half-layout step kernel");
+    else
+        QCHECK(c, launch_step(c->M, c->form, a, c->st), "step kernel");
     if (rp) QCHECK(c, launch_rho_reduce(c->d_partial, a.grid, c->M2, rho_slot, c->st), "rho reduce kernel");
     return QUAPI_OK;
 }
@@ -428,6 +436,12 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
 quapi_status run_grow_op(quapi_ctx* c, const OpPlan& gp, const void* A_in, void* A_out) {
     int sh = 0;
     while ((int64_t(1) << sh) < gp.lo_size) ++sh;
+    if (c->herm) {
+        QCHECK(c, launch_herm_grow(c->form, A_in, A_out, gp.n_in, c->d_tables + gp.off_lo, c->d_tables + gp.off_hi,
+                                   gp.lo_size, sh, c->st),
+               "half-layout grow kernel");
+        return QUAPI_OK;
+    }
     QCHECK(c, launch_grow(c->M, c->form, A_in, A_out, ipow(c->M2, gp.n_in), c->d_tables + gp.off_lo,
                           c->d_tables + gp.off_hi, gp.lo_size, sh, c->st),
            "grow kernel");
@@ -511,12 +525,16 @@ quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int6
     }
     c->state_n = -1;
     if (N == 0) return QUAPI_OK;
-    QCHECK(c, launch_init_tensor(rho0_dev, c->d_eta, eta_self0(c->L), c->d_s, c->M, c->form, c->buf[0], c->st),
+    QCHECK(c, launch_init_tensor(rho0_dev, c->d_eta, eta_self0(c->L), c->d_s, c->M, c->form, c->buf[0], c->st,
+                                 c->herm ? 1 : 0),
            "init tensor kernel");
     return run_steps(c, 0, 0, steps, nsteps, next, slots);
 }
 
-int64_t state_elements(const quapi_ctx* c, int64_t n) { return ipow(c->M2, (int)std::min<int64_t>(n + 1, c->L)); }
+int64_t state_elements(const quapi_ctx* c, int64_t n) {
+    const int d = (int)std::min<int64_t>(n + 1, c->L);
+    return c->herm ? half_entries(d) : ipow(c->M2, d);
+}
 
 quapi_status ensure_slots(quapi_ctx* c, int nsteps) {
     if (c->slots_cap < (size_t)nsteps) {
@@ -553,6 +571,7 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     a->use_tma = c->use_tma;
     a->stages = c->stages;
     a->err_flag = c->d_err;
+    a->half_digits = c->herm ? rp->n_in - 1 : -1;
     *M = c->M;
     *form = c->form;
     *st = c->st;
@@ -596,6 +615,7 @@ quapi_status batch_describe(const quapi_ctx* c, int64_t N, BatchInst* inst, int*
 }
 
 uint64_t ctx_uid(const quapi_ctx* c) { return c->uid; }
+bool ctx_half_layout(const quapi_ctx* c) { return c->herm; }
 bool ctx_tune_requested(const quapi_ctx* c) { return c->tune; }
 
 quapi_status record_error(const quapi_ctx* c, quapi_status st, const char* msg) {
@@ -654,6 +674,15 @@ quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const in
 quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* steps, int nsteps, double* rho_out) {
     if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
     if (!rho0 || !rho_out) return fail(c, QUAPI_ERR_ARG, "rho0 and rho_out must not be NULL");
+    if (c->herm) {
+        for (int r = 0; r < c->M; ++r)
+            for (int q = 0; q < c->M; ++q) {
+                const double* a = rho0 + 2 * (r * c->M + q);
+                const double* b = rho0 + 2 * (q * c->M + r);
+                if (std::fabs(a[0] - b[0]) > 1e-12 || std::fabs(a[1] + b[1]) > 1e-12)
+                    return fail(c, QUAPI_ERR_ARG, "the Hermitian half layout needs a Hermitian rho0");
+            }
+    }
     quapi_status s = check_steps(c, steps, nsteps);
     if (s != QUAPI_OK) return s;
     s = ensure_slots(c, nsteps);

@@ -225,15 +225,19 @@ struct StepArgs {
     bool use_tma;         // M = 2: stage input tiles with 2-D TMA copies when the tensor allows it
     int stages;           // TMA ring depth (2, 3, 4 or 6)
     int* err_flag;        // set to 1 by a CTA whose bounded wait expired
+    int half_digits;      // Hermitian half layout: digits of the fiber prefix (n_in - 1)
 };
 
 cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st);  // sets a.grid
 cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t S, const void* lo,
                         const void* hi, int64_t lo_size, int lo_shift, cudaStream_t st);
+cudaError_t launch_herm_step(int form, StepArgs& a, cudaStream_t st);  // sets a.grid
+cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
+                             int64_t lo_size, int lo_shift, cudaStream_t st);
 cudaError_t launch_rho_reduce(const double2* partial, int nparts, int M2, double2* rho_out,
                               cudaStream_t st);
 cudaError_t launch_init_tensor(const double2* rho0_dev, const double2* eta, int self0_idx,
-                               const double* s, int M, int form, void* A_out, cudaStream_t st);
+                               const double* s, int M, int form, void* A_out, cudaStream_t st, int herm = 0);
 int num_sms();
 
 // process-wide count of kernel launches issued by this library
@@ -283,6 +287,7 @@ struct BatchInst {
 
 uint64_t ctx_uid(const ::quapi_ctx* c);            // unique per context for the process lifetime
 bool ctx_tune_requested(const ::quapi_ctx* c);     // quapi_opts.tune was set
+bool ctx_half_layout(const ::quapi_ctx* c);        // tensors in the Hermitian half layout
 void batch_forget(uint64_t uid);                    // drop cached batch plans using that context
 
 // Fill inst with the tables and tensors of context c for a run to step N (host side).

@@ -93,11 +93,17 @@ __global__ void propagator_kernel(const double2* __restrict__ H, int M, double d
     }
 }
 
+// herm: write the Hermitian half layout of one digit (M = 2): entries x = 1, 0, 3
 __global__ void init_tensor_kernel(const double2* __restrict__ rho0, const double2* __restrict__ eta,
-                                   int self0_idx, const double* __restrict__ s, int M, int form,
-                                   void* A_out) {
+                                   int self0_idx, const double* __restrict__ s, int M, int form, int herm,
+                                   void* A_out_base) {
     int x = threadIdx.x;
     if (x >= M * M) return;
+    int pos = x;
+    if (herm) {
+        if (x == 2) return;
+        pos = (x == 1) ? 0 : (x == 0 ? 1 : 2);
+    }
     double sp = s[x / M], sm = s[x % M];
     double d = sp - sm;
     double2 e = eta[self0_idx];
@@ -105,14 +111,14 @@ __global__ void init_tensor_kernel(const double2* __restrict__ rho0, const doubl
     double2 z = make_double2(-d * (e.x * sp - e.x * sm), -d * (e.y * sp + e.y * sm));
     double2 v = cmul(rho0[x], cexp_d(z));
     if (form == QUAPI_FP64) {
-        reinterpret_cast<double2*>(A_out)[x] = v;
+        reinterpret_cast<double2*>(A_out_base)[pos] = v;
     } else if (form == QUAPI_DF64) {
         df2 r;
         r.h = make_float2((float)v.x, (float)v.y);
         r.l = make_float2((float)(v.x - (double)r.h.x), (float)(v.y - (double)r.h.y));
-        reinterpret_cast<df2*>(A_out)[x] = r;
+        reinterpret_cast<df2*>(A_out_base)[pos] = r;
     } else {
-        reinterpret_cast<float2*>(A_out)[x] = make_float2((float)v.x, (float)v.y);
+        reinterpret_cast<float2*>(A_out_base)[pos] = make_float2((float)v.x, (float)v.y);
     }
 }
 
@@ -214,8 +220,8 @@ cudaError_t launch_propagator(const double2* H_dev, int M, double dt, double2* U
 }
 
 cudaError_t launch_init_tensor(const double2* rho0_dev, const double2* eta, int self0_idx,
-                               const double* s, int M, int form, void* A_out, cudaStream_t st) {
-    init_tensor_kernel<<<1, 32, 0, st>>>(rho0_dev, eta, self0_idx, s, M, form, A_out);
+                               const double* s, int M, int form, void* A_out, cudaStream_t st, int herm) {
+    init_tensor_kernel<<<1, 32, 0, st>>>(rho0_dev, eta, self0_idx, s, M, form, herm, A_out);
     count_launch();
     return cudaGetLastError();
 }

@@ -51,7 +51,8 @@ class quapi_spectral(ctypes.Structure):
 class quapi_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("endpoint_mode", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("tune", ctypes.c_int),
-                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("hermitian", ctypes.c_int)]
 
 
 class QuapiError(RuntimeError):
@@ -142,7 +143,7 @@ def _stream_handle(stream):
 
 
 def quapi_opts_init(precision=QUAPI_FP64, endpoint_mode=QUAPI_ENDPOINT_STRANG, cuda_stream=None,
-                    tune=0, workspace=None, workspace_bytes=0) -> quapi_opts:
+                    tune=0, workspace=None, workspace_bytes=0, hermitian=0) -> quapi_opts:
     o = quapi_opts()
     load().quapi_opts_init(ctypes.byref(o))
     o.precision = int(precision)
@@ -151,6 +152,7 @@ def quapi_opts_init(precision=QUAPI_FP64, endpoint_mode=QUAPI_ENDPOINT_STRANG, c
     o.tune = int(tune)
     o.workspace = _dev_ptr(workspace)
     o.workspace_bytes = int(workspace_bytes)
+    o.hermitian = int(hermitian)
     return o
 
 

@@ -1,0 +1,126 @@
+"""The Hermitian half layout on the GPU against the oracle (full tensors converted on the host)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.recurrence as rec
+from oracle.eta import Spectral
+from paper_1205_6872_gb300 import layout as ly
+from paper_1205_6872_gb300 import workloads as wl
+from test_gpu_parity import _empty_dev, _from_dev, _to_dev, representable
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = {64: 1e-12, 32: 1e-5, 48: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def q():
+    assert torch.cuda.is_available()
+    from paper_1205_6872_gb300 import quapi
+    quapi.load()
+    return quapi
+
+
+S2 = np.array([1.0, -1.0])
+H2 = np.array([[0.5, 1.0], [1.0, -0.5]], complex)
+
+
+@pytest.mark.parametrize("prec", [64, 32, 48])
+@pytest.mark.parametrize("L,n", [(6, 1), (6, 3), (6, 5), (6, 6), (6, 7), (1, 1), (1, 4), (2, 2), (9, 9), (9, 25)])
+def test_half_layout_single_step(q, L, n, prec):
+    eta = wl.random_eta(L, seed=300 + L + n)
+    etad = oracle.unpack_eta(eta, L)
+    K = oracle.pair_propagator_K(oracle.propagator_U(H2, 0.1))
+    n_in = min(n, L)
+    A = ly.symmetrize(wl.random_tensor(4 ** n_in, seed=n + 7 * L), n_in)
+    A = ly.from_half(representable(ly.to_half(A, n_in), prec), n_in)  # what the device stores
+    G, g, _, summed = rec.step_tables(etad, S2, K, L, n)
+    want = rec.apply_step(A, G, g, n_in, summed)
+    out_digits = n_in if summed else n_in + 1
+    Gr, gr, _ = rec.readout_tables(etad, S2, K, L, n)
+    want_rho = rec.apply_readout(A, Gr, gr, n_in)
+    ctx = q.quapi_setup_eta(S2, H2, eta, 0.1, L, q.quapi_opts_init(precision=prec, hermitian=1))
+    try:
+        dA = _to_dev(ly.to_half(A, n_in), prec)
+        dout = _empty_dev(ly.count(out_digits), prec)
+        drho = torch.zeros(4, dtype=torch.complex128, device="cuda")
+        q.quapi_step_device(ctx, n, dA, dout, drho)
+        drho2 = torch.zeros(4, dtype=torch.complex128, device="cuda")
+        q.quapi_readout_static(ctx, n, dA, drho2)
+        torch.cuda.synchronize()
+        got = _from_dev(dout, prec)
+        got_rho, got_rho2 = drho.cpu().numpy(), drho2.cpu().numpy()
+    finally:
+        q.quapi_destroy(ctx)
+    scale = np.abs(want).max() + 1.0
+    tol = 2e-6 if prec == 32 else 1e-13
+    assert np.abs(got - ly.to_half(want, out_digits)).max() <= tol * scale
+    rtol = (1e-6 if prec == 32 else 1e-13) * max(1.0, np.abs(want_rho).max())
+    assert np.abs(got_rho - want_rho).max() <= rtol
+    assert np.abs(got_rho2 - got_rho).max() <= rtol
+
+
+@pytest.mark.parametrize("prec", [64, 32, 48])
+def test_half_layout_propagation_small(q, prec):
+    p = wl.spin_boson_L6()
+    rho0 = np.array([[0.7, 0.2 - 0.3j], [0.2 + 0.3j, 0.3]])
+    steps = [0, 1, 2, 5, 6, 7, 30, 100]
+    want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, rho0, steps)
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                        q.quapi_opts_init(precision=prec, hermitian=1))
+    try:
+        got = q.quapi_propagate(ctx, rho0, steps, 2)
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate(ctx, np.array([[1, 1j], [1j, 0]]), steps, 2)   # not Hermitian
+        assert e.value.status == q.QUAPI_ERR_ARG
+    finally:
+        q.quapi_destroy(ctx)
+    for i, k in enumerate(steps):
+        assert np.abs(got[i] - want[k]).max() <= TOL[prec], k
+
+
+@pytest.mark.parametrize("prec", [64, 32, 48])
+def test_half_layout_bench_workload_against_stored_oracle(q, prec):
+    p = wl.spin_boson_L14()
+    with open(os.path.join(HERE, "golden", "spin_boson_L14.json")) as fh:
+        g = json.load(fh)
+    steps = [int(k) for k in g["steps"]]
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                        q.quapi_opts_init(precision=prec, hermitian=1))
+    try:
+        got = q.quapi_propagate(ctx, p.rho0, steps, 2)
+    finally:
+        q.quapi_destroy(ctx)
+    worst = max(float(np.abs(got[i] - np.array([complex(a, b) for a, b in g["rho"][str(k)]]).reshape(2, 2)).max())
+                for i, k in enumerate(steps))
+    print(f"spin_boson_L14 half layout precision {prec}: max abs error vs oracle = {worst:.3e}")
+    assert worst <= TOL[prec]
+
+
+def test_half_layout_checkpoint_and_rejections(q):
+    p = wl.spin_boson_L6()
+    c1 = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(hermitian=1))
+    c2 = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, q.quapi_opts_init(hermitian=1))
+    try:
+        q.quapi_propagate(c1, p.rho0, [12], 2)
+        n, state = q.quapi_get_state(c1)
+        assert n == 11 and state.nbytes == 16 * ly.count(6)
+        q.quapi_set_state(c2, n, state)
+        a = q.quapi_propagate_resume(c1, [40], 2)
+        b = q.quapi_propagate_resume(c2, [40], 2)
+        assert np.array_equal(a, b)
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate_batch([c1], [p.rho0], [10])
+        assert e.value.status == q.QUAPI_ERR_UNSUPPORTED
+    finally:
+        q.quapi_destroy(c1)
+        q.quapi_destroy(c2)
+    with pytest.raises(q.QuapiError) as e:
+        q.quapi_setup([-1, 0, 1], np.eye(3), "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 3, q.quapi_opts_init(hermitian=1))
+    assert e.value.status == q.QUAPI_ERR_UNSUPPORTED

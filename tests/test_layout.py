@@ -1,0 +1,60 @@
+"""The Hermitian half layout helpers (CPU): sizes, bijection, round trips, and the symmetry itself.
+
+The symmetry A(conj path) = conj(A(path)) is checked on oracle tensors: a
+Hermitian rho0 propagated by the oracle's recurrence yields tensors with it.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.recurrence as rec
+from oracle.eta import Spectral
+from paper_1205_6872_gb300 import layout as ly
+
+
+@pytest.mark.parametrize("n", range(0, 8))
+def test_half_layout_is_a_transversal_of_conjugation(n):
+    idx = ly.canonical_indices(n)
+    assert idx.size == ly.count(n) == (4 ** n + 2 ** n) // 2
+    assert np.unique(idx).size == idx.size
+    conj = ly.conj_index(np.arange(4 ** n), n)
+    assert np.array_equal(conj[conj], np.arange(4 ** n))        # an involution
+    canon = np.zeros(4 ** n, bool)
+    canon[idx] = True
+    # every index is canonical or has a canonical conjugate; both only when self-conjugate
+    assert np.all(canon | canon[conj])
+    both = canon & canon[conj]
+    assert np.array_equal(np.nonzero(both)[0], np.nonzero(conj == np.arange(4 ** n))[0])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_fibers_stay_contiguous(n):
+    """In the half layout of n digits, each last-digit fiber occupies consecutive positions."""
+    idx = ly.canonical_indices(n)
+    prefix = idx // 4
+    starts = np.nonzero(np.diff(prefix) != 0)[0] + 1
+    groups = np.split(prefix, starts)
+    assert all(np.all(g == g[0]) for g in groups)
+    assert len(groups) == ly.count(n - 1)
+
+
+def test_round_trip():
+    rng = np.random.default_rng(0)
+    for n in range(0, 6):
+        A = ly.symmetrize(rng.normal(size=4 ** n) + 1j * rng.normal(size=4 ** n), n)
+        assert np.allclose(ly.from_half(ly.to_half(A, n), n), A)
+
+
+def test_oracle_tensors_have_the_symmetry():
+    s = np.array([1.0, -1.0])
+    H = np.array([[0.3, 1.0], [1.0, -0.3]])
+    rho0 = np.array([[0.7, 0.2 - 0.3j], [0.2 + 0.3j, 0.3]])
+    run = oracle.OracleRun(s, H, Spectral("ohmic_exp", 0.4, 3.0), 1.0, 0.15, 5)
+    A = rec.initial_tensor(run.eta, s, rho0)
+    for n in range(1, 12):
+        G, g, n_in, summed = rec.step_tables(run.eta, s, run.K, 5, n)
+        A = rec.apply_step(A, G, g, n_in, summed)
+        digits = n_in if summed else n_in + 1
+        conj = ly.conj_index(np.arange(4 ** digits), digits)
+        assert np.abs(A[conj] - np.conj(A)).max() < 1e-14 * max(1.0, np.abs(A).max()), n
