@@ -85,14 +85,17 @@ typedef struct {
     int tune;               /* 0: default launch shape; 1: pick it by timing candidates (cached)   */
     void* workspace;        /* optional caller-owned device buffer for the tensors, or NULL        */
     size_t workspace_bytes; /* its size; must be >= quapi_query_memory()'s tensor_bytes            */
-    int hermitian;          /* 1: keep only the canonical half of A (M = 2; needs a Hermitian rho0).
+    int hermitian;          /* 1: keep only (about) half of A (M = 2; needs a Hermitian rho0).
                                Swapping s+ and s- at every path point conjugates a path's weight, so
-                               A(conj path) = conj(A(path)); the half layout stores, for n digits,
-                               [top digit 1: 4^(n-1) plain][top 0: half of n-1][top 3: half of n-1],
-                               (4^n + 2^n)/2 entries (point values 0=(+,+) 1=(+,-) 2=(-,+) 3=(-,-)).
-                               Tensors passed to quapi_step_device / quapi_readout_static and the
-                               checkpoint state then use this layout.  Not combinable with
-                               quapi_propagate_batch. */
+                               A(conj path) = conj(A(path)) (point values 0=(+,+) 1=(+,-) 2=(-,+)
+                               3=(-,-); conjugation swaps 1 and 2).  A prefix is canonical when its
+                               first digit outside {0,3} is a 1; canonical prefixes of n digits are
+                               ordered [top 1: 4^(n-1) plain][top 0: canonical n-1][top 3: canonical
+                               n-1].  An n-digit tensor then stores the 4-entry last-digit fiber of
+                               every canonical (n-1)-digit prefix, in that order: 2*4^(n-1) + 2^n
+                               entries, prefix c at entry 4c.  Tensors passed to quapi_step_device /
+                               quapi_readout_static and the checkpoint state use this layout.  Not
+                               combinable with quapi_propagate_batch. */
 } quapi_opts;
 
 /* Fill *opts with the defaults above. */

@@ -572,47 +572,67 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
 // ---- Hermitian half layout (M = 2) ------------------------------------------------
 //
 // For a Hermitian rho(0), A(conj path) = conj(A(path)) (swapping s+ and s- of
-// every point conjugates K and every influence factor).  Only canonical entries
-// are stored: an index is canonical when its most significant digit outside
-// {0, 3} is a 1.  Layout of n digits: [top 1: 4^(n-1) plain continuations]
-// [top 0: half layout of n-1 digits] [top 3: half layout of n-1 digits],
-// C(n) = (4^n + 2^n)/2 entries; every last-digit fiber stays contiguous
-// (4 entries, or 3 stored as 1, 0, 3 for a prefix of only 0s and 3s).
-// One thread per canonical prefix f computes the rows the half layout keeps:
-// (1, f), (1, conj f) from the same loaded fiber, and (0, f), (3, f); the
-// readout adds row 1 over f and conj f and twice the real part of the
-// diagonal rows (their conjugate partners are conjugates).
+// every point conjugates K and every influence factor).  A prefix is canonical
+// when its most significant digit outside {0, 3} is a 1; canonical n-digit
+// prefixes are ordered [top 1: 4^(n-1) plain][top 0: canonical n-1][top 3:
+// canonical n-1], C(n) = (4^n + 2^n)/2 of them.  An n-digit tensor stores the
+// 4-entry last-digit fiber of every canonical (n-1)-digit prefix, prefix c at
+// entry 4c (a prefix of only 0s and 3s keeps its redundant digit-2 entry, the
+// conjugate of its digit-1 entry).  One thread per canonical input prefix f
+// computes, from the one loaded fiber, the rows this layout keeps: (1, f),
+// (1, conj f), (0, f), (3, f) (and the conjugate entries (0/3, conj f) when
+// those are stored); the readout adds row 1 over f and conj f and twice the
+// real part of the diagonal rows (their conjugate partners are conjugates).
 
-__host__ __device__ __forceinline__ int64_t half_count(int n) {
+__host__ __device__ __forceinline__ int64_t half_count(int n) {  // C(n)
     return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1;
 }
+__host__ __device__ __forceinline__ int64_t half_entries(int n) {  // stored entries of n digits
+    return n == 0 ? 1 : 4 * half_count(n - 1);
+}
 
-// canonical position c of an n-digit half layout -> plain index, number of
-// self-conjugate entries before c, and whether c is self-conjugate
-__device__ __forceinline__ void half_decode(int64_t c, int n, uint32_t& plain, int64_t& sc_before, bool& sc) {
+// canonical position c among n-digit prefixes -> plain digits and whether the
+// prefix is its own conjugate (all digits 0 or 3).  32-bit: n <= 15.
+__device__ __forceinline__ uint32_t half_count32(int n) { return ((1u << (2 * n)) + (1u << n)) >> 1; }
+
+__device__ __forceinline__ void half_decode(uint32_t c, int n, uint32_t& plain, bool& sc) {
     uint32_t p = 0;
-    int64_t s = 0;
     for (int level = n; level >= 1; --level) {
-        const int64_t r1 = int64_t(1) << (2 * (level - 1));
+        const uint32_t r1 = 1u << (2 * (level - 1));
         if (c < r1) {  // digit 1, the rest is plain
-            plain = (p << (2 * level)) | (uint32_t(1) << (2 * (level - 1))) | (uint32_t)c;
-            sc_before = s;
+            plain = (p << (2 * level)) | r1 | c;
             sc = false;
             return;
         }
         c -= r1;
-        const int64_t cn1 = half_count(level - 1);
+        const uint32_t cn1 = half_count32(level - 1);
         if (c < cn1) {
-            p = (p << 2) | 0u;
+            p = p << 2;
         } else {
             c -= cn1;
-            s += int64_t(1) << (level - 1);
             p = (p << 2) | 3u;
         }
     }
     plain = p;
-    sc_before = s;
     sc = true;
+}
+
+// canonical position of a canonical n-digit prefix given by its plain digits
+__device__ __forceinline__ uint32_t half_position(uint32_t h, int n) {
+    uint32_t idx = 0;
+    for (int level = n; level >= 1; --level) {
+        const uint32_t d = (h >> (2 * (level - 1))) & 3u;
+        const uint32_t r1 = 1u << (2 * (level - 1));
+        if (d == 1u) return idx + (h & (r1 - 1u));
+        idx += r1;
+        if (d == 3u) idx += half_count32(level - 1);
+    }
+    return idx;
+}
+
+__device__ __forceinline__ bool self_conjugate(uint32_t h, int n) {  // every digit 0 or 3
+    const uint32_t mask = (n >= 16) ? 0x55555555u : ((1u << (2 * n)) - 1u) & 0x55555555u;
+    return ((h ^ (h >> 1)) & mask) == 0u;
 }
 
 __device__ __forceinline__ uint32_t conj_digits(uint32_t f) {
@@ -640,20 +660,34 @@ __device__ __forceinline__ df2 real_part(df2 v) {
     v.l.y = 0.f;
     return v;
 }
-__device__ __forceinline__ double2 ld_plain(const double2* p) { return __ldcs(p); }
-__device__ __forceinline__ float2 ld_plain(const float2* p) { return __ldcs(p); }
-__device__ __forceinline__ df2 ld_plain(const df2* p) { return ld_stream(p); }
 
-// outputs of rows 0, 1, 3 for one fiber a (row 2 is never stored)
-template <int FORM, bool DIAG, bool END>
+// the 4 entries of fiber c (aligned: FP32 as two 16-byte loads)
+template <int FORM>
+__device__ __forceinline__ void load_fiber4(const typename FormT<FORM>::Elem* __restrict__ A, uint32_t c,
+                                            typename FormT<FORM>::Elem (&a)[4]) {
+    if constexpr (FORM == QUAPI_FP32) {
+        const float4* p = reinterpret_cast<const float4*>(A + 4ull * c);
+        const float4 v0 = __ldcs(p), v1 = __ldcs(p + 1);
+        a[0] = make_float2(v0.x, v0.y);
+        a[1] = make_float2(v0.z, v0.w);
+        a[2] = make_float2(v1.x, v1.y);
+        a[3] = make_float2(v1.z, v1.w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = ld_stream(A + 4ull * c + q);
+    }
+}
+
+// outputs of rows 0, 1, 3 for one fiber a (row 2 is never needed); ONLY1: row 1 alone
+template <int FORM, bool DIAG, bool END, bool ONLY1 = false>
 __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const typename FormT<FORM>::Elem (&a)[4],
                                           uint32_t f, typename FormT<FORM>::Elem (&o)[4]) {
-    using Tab = typename FormT<FORM>::Tab;
     const uint32_t fh = f >> T.lo_shift, fl = f & (T.lo_size - 1u);
-    const Tab* isum = END ? T.isume : T.isum;
-    const Tab* lo = END ? T.loe : T.lo;
-    const Tab* hi = END ? T.hie : T.hi;
-    if (DIAG) {
+    const auto* isum = END ? T.isume : T.isum;
+    const auto* lo = END ? T.loe : T.lo;
+    const auto* hi = END ? T.hie : T.hi;
+    if (ONLY1) {
+    } else if (DIAG) {
         const auto S = plain_sum<4>(a);
         o[0] = apply_hi(hi[fh], S);
         o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
@@ -667,6 +701,7 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
 template <int FORM, bool WRITE, bool READ, bool DIAG>
 __global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
     using Elem = typename FormT<FORM>::Elem;
+    constexpr int U = 1;  // prefixes per thread per iteration
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepTables<2, FORM> T;
     T.template stage<WRITE, READ>(args, smem_raw);
@@ -676,54 +711,67 @@ __global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
     for (int x = 0; x < 4; ++x) racc[x].init();
     const Elem* __restrict__ A = reinterpret_cast<const Elem*>(args.A_in);
     Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
-    const int npre_digits = args.half_digits;  // digits of the prefix f (n_in - 1)
-    const int64_t npre = half_count(npre_digits);
-    const int64_t F = args.F;                  // 4^(n_in - 1): size of the plain row-1 block
+    const int np = args.half_digits;           // digits of the prefix f (n_in - 1); 32-bit indices (np <= 15)
+    const uint32_t npre = half_count32(np);
+    const uint32_t top = (np >= 1) ? (1u << (2 * (np - 1))) : 0u;   // 4^(np-1)
+    const uint32_t cnh = (np >= 1) ? half_count32(np - 1) : 0u;
     constexpr int remap[4] = {0, 2, 1, 3};
-    for (int64_t c = (int64_t)blockIdx.x * kThreads + threadIdx.x; c < npre; c += (int64_t)gridDim.x * kThreads) {
-        uint32_t f;
-        int64_t s;
-        bool sc;
-        half_decode(c, npre_digits, f, s, sc);
-        const int64_t pin = 4 * c - s;
-        Elem a[4], b[4];
-        if (!sc) {
+    for (uint32_t c0 = (blockIdx.x * kThreads + threadIdx.x) * U; c0 < npre; c0 += gridDim.x * kThreads * U) {
+        Elem a[U][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = ld_plain(A + pin + q);
-        } else {  // stored as old = 1, 0, 3; old = 2 is the conjugate of old = 1
-            a[1] = ld_plain(A + pin);
-            a[0] = ld_plain(A + pin + 1);
-            a[3] = ld_plain(A + pin + 2);
-            a[2] = conjv(a[1]);
-        }
+        for (int u = 0; u < U; ++u)
+            if (c0 + u < npre) load_fiber4<FORM>(A, c0 + u, a[u]);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b[q] = conjv(a[remap[q]]);  // fiber of the conjugate prefix
-        const uint32_t fb = conj_digits(f);
-        if (WRITE) {
-            Elem o[4];
-            herm_rows<FORM, DIAG, false>(T, a, f, o);
-            st_stream(out + f, o[1]);
-            st_stream(out + F + c, o[0]);
-            st_stream(out + F + npre + c, o[3]);
-            if (!sc) {
-                Elem ob[4];
-                herm_rows<FORM, DIAG, false>(T, b, fb, ob);
-                st_stream(out + fb, ob[1]);
+        for (int u = 0; u < U; ++u) {
+            const uint32_t c = c0 + u;
+            if (c >= npre) break;
+            uint32_t f;
+            bool sc;
+            half_decode(c, np, f, sc);
+            Elem b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = conjv(a[u][remap[q]]);  // fiber of the conjugate prefix
+            const uint32_t fb = conj_digits(f);
+            if (WRITE) {
+                Elem o[4];
+                herm_rows<FORM, DIAG, false>(T, a[u], f, o);
+                if (np == 0) {  // one-digit output: every point stored
+                    st_stream(out + 0, o[0]);
+                    st_stream(out + 1, o[1]);
+                    st_stream(out + 2, conjv(o[1]));
+                    st_stream(out + 3, o[3]);
+                } else {
+                    const uint32_t fl = f & 3u, fh = f >> 2;
+                    const uint32_t h = half_position(fh, np - 1);
+                    const uint32_t b0 = 4u * (top + h), b3 = 4u * (top + cnh + h);
+                    st_stream(out + f, o[1]);
+                    st_stream(out + b0 + fl, o[0]);
+                    st_stream(out + b3 + fl, o[3]);
+                    if (!sc) {
+                        Elem ob[4];
+                        herm_rows<FORM, DIAG, false, true>(T, b, fb, ob);
+                        st_stream(out + fb, ob[1]);
+                        if (self_conjugate(fh, np - 1)) {  // (0/3, fh, 2) are stored too: conjugates of (0/3, f)
+                            st_stream(out + b0 + 2, conjv(o[0]));
+                            st_stream(out + b3 + 2, conjv(o[3]));
+                        }
+                    }
+                }
             }
-        }
-        if (READ) {
-            Elem r[4];
-            herm_rows<FORM, DIAG, true>(T, a, f, r);
-            racc[1].add(r[1]);
-            if (!sc) {
-                Elem rb[4];
-                herm_rows<FORM, DIAG, true>(T, b, fb, rb);
-                racc[1].add(rb[1]);
-                racc[0].add(twice_real(r[0]));
-                racc[3].add(twice_real(r[3]));
-            } else {
-                racc[0].add(real_part(r[0]));
-                racc[3].add(real_part(r[3]));
+            if (READ) {
+                Elem r[4];
+                herm_rows<FORM, DIAG, true>(T, a[u], f, r);
+                racc[1].add(r[1]);
+                if (!sc) {
+                    Elem rb[4];
+                    herm_rows<FORM, DIAG, true, true>(T, b, fb, rb);
+                    racc[1].add(rb[1]);
+                    racc[0].add(twice_real(r[0]));
+                    racc[3].add(twice_real(r[3]));
+                } else {
+                    racc[0].add(real_part(r[0]));
+                    racc[3].add(real_part(r[3]));
+                }
             }
         }
     }
@@ -752,7 +800,7 @@ __global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
     }
 }
 
-// growth in the half layout: input n_in digits (C(n_in) entries) -> n_in + 1 digits
+// growth in the half layout: input n_in digits -> n_in + 1 digits, one thread per stored entry
 template <int FORM>
 __global__ void __launch_bounds__(kThreads) herm_grow_kernel(const void* __restrict__ A_in_, void* __restrict__ A_out_,
                                                              int n_in, const void* __restrict__ lo_,
@@ -764,26 +812,31 @@ __global__ void __launch_bounds__(kThreads) herm_grow_kernel(const void* __restr
     Elem* out = reinterpret_cast<Elem*>(A_out_);
     const Tab* lo = reinterpret_cast<const Tab*>(lo_);
     const Tab* hi = reinterpret_cast<const Tab*>(hi_);
-    const int64_t S = int64_t(1) << (2 * n_in);
-    const int64_t Cn = half_count(n_in);
+    const int64_t S = int64_t(1) << (2 * n_in);          // plain row-1 block of the output
+    const int64_t Cp = half_count(n_in - 1);             // canonical prefixes of the input
+    const int64_t entries = 4 * Cp;
     const uint32_t lo_size = (uint32_t)lo_size_;
     const int64_t hi_size = S / lo_size_;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Cn; c += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t i;
-        int64_t s;
-        bool sc;
-        half_decode(c, n_in, i, s, sc);
-        const Elem v = A[c];
-        auto P = [&](int x, uint32_t idx, Elem w) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < entries; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e >> 2;
+        const uint32_t d = (uint32_t)(e & 3);
+        uint32_t P;
+        bool scP;
+        half_decode((uint32_t)c, n_in - 1, P, scP);
+        const uint32_t i = (P << 2) | d;
+        const Elem v = A[e];
+        auto Pm = [&](int x, uint32_t idx, Elem w) {
             return tmul(hi[(int64_t)x * hi_size + (idx >> lo_shift)], tmul(lo[(int64_t)x * lo_size + (idx & (lo_size - 1u))], w));
         };
-        out[i] = P(1, i, v);
-        if (!sc) {
-            const uint32_t ib = conj_digits(i);
-            out[ib] = P(1, ib, conjv(v));
+        if (!(scP && d == 2u)) {  // (P, 2) of a self-conjugate P is written from (P, 1)
+            out[i] = Pm(1, i, v);
+            if (!(scP && (d == 0u || d == 3u))) {
+                const uint32_t ib = conj_digits(i);
+                out[ib] = Pm(1, ib, conjv(v));
+            }
         }
-        out[S + c] = P(0, i, v);
-        out[S + Cn + c] = P(3, i, v);
+        out[4 * ((S >> 2) + c) + d] = Pm(0, i, v);
+        out[4 * ((S >> 2) + Cp + c) + d] = Pm(3, i, v);
     }
 }
 
@@ -974,7 +1027,8 @@ cudaError_t launch_herm_variant(StepArgs& a, cudaStream_t st) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
-    const int64_t work = (half_count(a.half_digits) + kThreads - 1) / kThreads;
+    const int U = 1;
+    const int64_t work = (half_count(a.half_digits) + (int64_t)kThreads * U - 1) / ((int64_t)kThreads * U);
     int64_t g = (int64_t)num_sms() * (occ < 1 ? 1 : occ);
     if (g > work) g = work;
     if (g > a.grid) g = a.grid;
@@ -1009,7 +1063,7 @@ cudaError_t launch_herm_step(int form, StepArgs& a, cudaStream_t st) {
 
 cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
                              int64_t lo_size, int lo_shift, cudaStream_t st) {
-    const int64_t Cn = half_count(n_in);
+    const int64_t Cn = half_entries(n_in);
     int64_t blocks = (Cn + kThreads - 1) / kThreads;
     if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
     if (blocks < 1) blocks = 1;

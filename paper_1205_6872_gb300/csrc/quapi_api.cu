@@ -53,7 +53,11 @@ int64_t ipow(int64_t b, int e) {
 }
 
 int max_dkmax(int M) { return M == 2 ? 16 : 10; }
-int64_t half_entries(int n) { return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1; }
+// stored entries of an n-digit tensor in the Hermitian half layout: 4 C(n-1), C(m) = (4^m + 2^m)/2
+int64_t half_entries(int n) {
+    if (n == 0) return 1;
+    return 4 * (((int64_t(1) << (2 * (n - 1))) + (int64_t(1) << (n - 1))) >> 1);
+}
 int lo_digits_max(int M) { return M == 2 ? 4 : 2; }
 
 }  // namespace

@@ -93,17 +93,13 @@ __global__ void propagator_kernel(const double2* __restrict__ H, int M, double d
     }
 }
 
-// herm: write the Hermitian half layout of one digit (M = 2): entries x = 1, 0, 3
 __global__ void init_tensor_kernel(const double2* __restrict__ rho0, const double2* __restrict__ eta,
                                    int self0_idx, const double* __restrict__ s, int M, int form, int herm,
                                    void* A_out_base) {
     int x = threadIdx.x;
     if (x >= M * M) return;
-    int pos = x;
-    if (herm) {
-        if (x == 2) return;
-        pos = (x == 1) ? 0 : (x == 0 ? 1 : 2);
-    }
+    const int pos = x;  // one digit: the half layout stores every point too
+    (void)herm;
     double sp = s[x / M], sm = s[x % M];
     double d = sp - sm;
     double2 e = eta[self0_idx];

@@ -32,7 +32,8 @@ H2 = np.array([[0.5, 1.0], [1.0, -0.5]], complex)
 
 
 @pytest.mark.parametrize("prec", [64, 32, 48])
-@pytest.mark.parametrize("L,n", [(6, 1), (6, 3), (6, 5), (6, 6), (6, 7), (1, 1), (1, 4), (2, 2), (9, 9), (9, 25)])
+@pytest.mark.parametrize("L,n", [(6, 1), (6, 3), (6, 5), (6, 6), (6, 7), (1, 1), (1, 4), (2, 2), (9, 9), (9, 25),
+                                 (10, 12), (11, 11), (11, 14)])
 def test_half_layout_single_step(q, L, n, prec):
     eta = wl.random_eta(L, seed=300 + L + n)
     etad = oracle.unpack_eta(eta, L)

@@ -14,9 +14,9 @@ from paper_1205_6872_gb300 import layout as ly
 
 
 @pytest.mark.parametrize("n", range(0, 8))
-def test_half_layout_is_a_transversal_of_conjugation(n):
-    idx = ly.canonical_indices(n)
-    assert idx.size == ly.count(n) == (4 ** n + 2 ** n) // 2
+def test_canonical_order_is_a_transversal_of_conjugation(n):
+    idx = ly.canonical_order(n)
+    assert idx.size == ly.canonical_count(n) == (4 ** n + 2 ** n) // 2
     assert np.unique(idx).size == idx.size
     conj = ly.conj_index(np.arange(4 ** n), n)
     assert np.array_equal(conj[conj], np.arange(4 ** n))        # an involution
@@ -28,15 +28,17 @@ def test_half_layout_is_a_transversal_of_conjugation(n):
     assert np.array_equal(np.nonzero(both)[0], np.nonzero(conj == np.arange(4 ** n))[0])
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 5])
-def test_fibers_stay_contiguous(n):
-    """In the half layout of n digits, each last-digit fiber occupies consecutive positions."""
+@pytest.mark.parametrize("n", range(1, 8))
+def test_device_layout_covers_every_index_up_to_conjugation(n):
     idx = ly.canonical_indices(n)
-    prefix = idx // 4
-    starts = np.nonzero(np.diff(prefix) != 0)[0] + 1
-    groups = np.split(prefix, starts)
-    assert all(np.all(g == g[0]) for g in groups)
-    assert len(groups) == ly.count(n - 1)
+    assert idx.size == ly.count(n) == 2 * 4 ** (n - 1) + 2 ** n
+    assert np.unique(idx).size == idx.size
+    conj = ly.conj_index(np.arange(4 ** n), n)
+    stored = np.zeros(4 ** n, bool)
+    stored[idx] = True
+    assert np.all(stored | stored[conj])
+    # fibers: prefix c occupies entries 4c .. 4c+3, last digits 0..3 in order
+    assert np.array_equal(idx.reshape(-1, 4) % 4, np.tile(np.arange(4), (ly.canonical_count(n - 1), 1)))
 
 
 def test_round_trip():
