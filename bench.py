@@ -5,12 +5,15 @@ workload (M=2, Delta k_max=14: 4^14 = 268,435,456 tensor entries; Ohmic alpha=0.
 wc=2.5, beta=0.5, dt=0.15, 1000 steps, rho read out at the final step only):
 growth phase, 987 fused steady-state steps, the final readout.
 
-Metric: tensor element-updates/s = (M^2)^L entries x (N - L + 1) full-tensor
-passes / time.  value: FP32 form, tables and rho0 resident on the device
-(quapi_propagate_device); e2e: the public host API per step (quapi_setup from
-host arrays + quapi_propagate to host rho + quapi_destroy).  forms.fp64: the
-plain FP64 form on the same workload.  roofline: the dominant kernel (the
-fused steady-state step) timed alone with CUDA events on its stream.
+Metric: tensor element-updates/s = (M^2)^L logical entries x (N - L + 1)
+full-tensor passes / time.  value: FP32 form in the Hermitian half layout,
+tables and rho0 resident on the device (quapi_propagate_device); e2e: the
+public host API per step (quapi_setup from host arrays + quapi_propagate to
+host rho + quapi_destroy).  forms: the full layout, the plain FP64 form (the
+baseline the other forms' speedups refer to) and the DF64 form.  roofline:
+the dominant kernel (the fused steady-state step) timed alone with CUDA
+events on its stream; algorithmic bytes = one read and one write of every
+stored entry.
 
 --impl reference: the FP64 CPU oracle on the host cores, a bounded sample of
 the same workload per step (a few steady-state steps on a full-size tensor).
@@ -32,7 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "QUAPI tensor element-updates/s (M=2, dkmax=14; FP32 form, FP64 form in forms.fp64)"
+METRIC = "QUAPI tensor element-updates/s (M=2, dkmax=14; FP32 form; FP64 / DF64 forms and full layout in forms)"
 UNIT = "element-updates/s"
 WORKLOAD = "spin_boson_L14"
 
@@ -146,8 +149,17 @@ def element_updates(p):
     return float((p.M * p.M) ** p.L) * float(p.N - p.L + 1)
 
 
-def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None):
-    opts = q.quapi_opts_init(precision=precision, cuda_stream=stream)
+def tensor_entries(p, half):
+    from paper_1205_6872_gb300 import layout
+    return layout.count(p.L) if half else (p.M * p.M) ** p.L
+
+
+def entry_bytes(q, precision):
+    return 8 if precision == q.QUAPI_FP32 else 16
+
+
+def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None, half=False):
+    opts = q.quapi_opts_init(precision=precision, cuda_stream=stream, hermitian=int(half))
     ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, opts)
     try:
         rho0 = torch.tensor(np.asarray(p.rho0).reshape(-1), dtype=torch.complex128, device="cuda")
@@ -176,7 +188,7 @@ def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None
         ms = max_over_ranks(ms, world)
         rho_final = rho.cpu().numpy().reshape(p.M, p.M)
         # dominant kernel alone: the fused steady-state step on a full tensor
-        n_el = (p.M * p.M) ** p.L
+        n_el = tensor_entries(p, half)
         dt_ = torch.complex64 if precision == 32 else torch.complex128
         gen = torch.Generator(device="cuda").manual_seed(1)
         A = torch.randn(n_el, dtype=dt_, device="cuda", generator=gen)
@@ -199,14 +211,16 @@ def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None
         torch.cuda.empty_cache()
     finally:
         q.quapi_destroy(ctx)
-    return dict(ms=ms, launches=launches, clocks=clocks, rho=rho_final, kernel_ms=kern_ms)
+    algo = 2.0 * tensor_entries(p, half) * entry_bytes(q, precision)  # one read and one write per stored entry
+    return dict(ms=ms, launches=launches, clocks=clocks, rho=rho_final, kernel_ms=kern_ms, bytes=algo,
+                kernel_GBps=algo / (kern_ms / 1e3) / 1e9)
 
 
-def time_e2e(q, torch, p, precision, steps, warmup):
+def time_e2e(q, torch, p, precision, steps, warmup, half=False):
     """Public host API per step: setup from host arrays, propagate to host rho, destroy."""
     def one():
         ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
-                            q.quapi_opts_init(precision=precision))
+                            q.quapi_opts_init(precision=precision, hermitian=int(half)))
         try:
             return q.quapi_propagate(ctx, p.rho0, [p.N], p.M)
         finally:
@@ -428,50 +442,63 @@ def main():
     p = wl.spin_boson_L14()
     stream = torch.cuda.Stream()
     sampler = ClockSampler(local)
-    r32 = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, sampler)
     ups = element_updates(p)
-    value = world * ups / (r32["ms"] / 1000.0)
+    peak, peak_kind = measured_peaks()
+
+    def form_entry(r, layout_name, ref=None):
+        d = dict(value=world * ups / (r["ms"] / 1000.0), unit=UNIT, ms_per_step=r["ms"], layout=layout_name,
+                 kernel_ms=r["kernel_ms"], kernel_GBps=r["kernel_GBps"], kernel_frac_of_hbm=r["kernel_GBps"] / peak,
+                 rho_final=[[float(z.real), float(z.imag)] for z in r["rho"].reshape(-1)])
+        if ref is not None:
+            d["max_abs_vs_fp64_full"] = float(np.abs(r["rho"] - ref["rho"]).max())
+        return d
+
+    # headline: FP32 form, Hermitian half layout (the fastest configuration for a Hermitian rho0)
+    r32h = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, sampler, half=True)
+    value = world * ups / (r32h["ms"] / 1000.0)
     forms = {}
+    r32f = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, half=False)
+    forms["fp32_full"] = form_entry(r32f, "full")
     if not args.no_fp64:
-        r64 = time_form(q, torch, p, q.QUAPI_FP64, args.steps, args.warmup, stream, world)
-        forms["fp64"] = dict(value=world * ups / (r64["ms"] / 1000.0), unit=UNIT, ms_per_step=r64["ms"],
-                             kernel_ms=r64["kernel_ms"], rho_final=[[float(z.real), float(z.imag)]
-                                                                    for z in r64["rho"].reshape(-1)])
-        forms["fp64"]["fp32_vs_fp64_max_abs"] = float(np.abs(r32["rho"] - r64["rho"]).max())
-        forms["fp64"]["speedup_fp32_over_fp64"] = r64["ms"] / r32["ms"]
-        forms["fp64"]["roofline"] = dict(bound="alu", unit="GB/s",
-                                         achieved=32.0 * (p.M * p.M) ** p.L / (r64["kernel_ms"] / 1e3) / 1e9,
-                                         note="FP64 pipe saturated (DFMA 1.2 TFLOP/s on this part)")
-        rdf = time_form(q, torch, p, q.QUAPI_DF64, args.steps, args.warmup, stream, world)
-        forms["df64"] = dict(value=world * ups / (rdf["ms"] / 1000.0), unit=UNIT, ms_per_step=rdf["ms"],
-                             kernel_ms=rdf["kernel_ms"],
-                             kernel_GBps=32.0 * (p.M * p.M) ** p.L / (rdf["kernel_ms"] / 1e3) / 1e9,
-                             df64_vs_fp64_max_abs=float(np.abs(rdf["rho"] - r64["rho"]).max()),
-                             speedup_df64_over_fp64=r64["ms"] / rdf["ms"])
+        r64f = time_form(q, torch, p, q.QUAPI_FP64, args.steps, args.warmup, stream, world, half=False)
+        forms["fp64_full"] = form_entry(r64f, "full")
+        forms["fp64_full"]["bound"] = "alu (FP64 pipe saturated; DFMA 1.2 TFLOP/s on this part)"
+        r64h = time_form(q, torch, p, q.QUAPI_FP64, args.steps, args.warmup, stream, world, half=True)
+        forms["fp64_half"] = form_entry(r64h, "half", r64f)
+        rdff = time_form(q, torch, p, q.QUAPI_DF64, args.steps, args.warmup, stream, world, half=False)
+        forms["df64_full"] = form_entry(rdff, "full", r64f)
+        rdfh = time_form(q, torch, p, q.QUAPI_DF64, args.steps, args.warmup, stream, world, half=True)
+        forms["df64_half"] = form_entry(rdfh, "half", r64f)
+        forms["fp32_full"]["max_abs_vs_fp64_full"] = float(np.abs(r32f["rho"] - r64f["rho"]).max())
+        forms["speedups_over_plain_fp64"] = dict(
+            fp32_half=r64f["ms"] / r32h["ms"], fp32_full=r64f["ms"] / r32f["ms"],
+            df64_half=r64f["ms"] / rdfh["ms"], df64_full=r64f["ms"] / rdff["ms"], fp64_half=r64f["ms"] / r64h["ms"])
+        headline_vs_fp64 = float(np.abs(r32h["rho"] - r64f["rho"]).max())
+    else:
+        headline_vs_fp64 = None
     if not args.no_batched:
         forms["batched_256_fp32"] = time_batched(q, torch, args.steps, args.warmup, world, rank)
-    e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1))
+    e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1), half=True)
     e2e_s = max_over_ranks(e2e_s, world)
-    peak, peak_kind = measured_peaks()
-    bytes_per_launch = 16.0 * (p.M * p.M) ** p.L  # FP32: 8 B read + 8 B written per entry
-    achieved = bytes_per_launch / (r32["kernel_ms"] / 1000.0) / 1e9
-    traffic = recorded_traffic("step_kernel_fp32_m2")
+    achieved = r32h["kernel_GBps"]
+    traffic = recorded_traffic("herm_step_kernel_fp32_m2")
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-        ms_per_step=r32["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        ms_per_step=r32h["ms"], higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic",
-        config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, form="fp32", readout="justFinalPoint",
-                    parallelism=f"replicas{world}",
-                    l2="inputs larger than L2: each step streams two 2.1 GB tensors"),
+        config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, form="fp32", layout="hermitian half",
+                    readout="justFinalPoint", parallelism=f"replicas{world}",
+                    l2="inputs larger than L2: each step streams two 1.07 GB tensors"),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                      traffic=traffic, peak_source=peak_kind, kernel="step_kernel<M=2,FP32>",
-                      kernel_ms=r32["kernel_ms"], algorithmic_bytes_per_launch=bytes_per_launch),
+                      traffic=traffic, peak_source=peak_kind, kernel="herm_step_kernel<FP32> (half layout)",
+                      kernel_ms=r32h["kernel_ms"], algorithmic_bytes_per_launch=r32h["bytes"]),
         e2e=dict(value=world * ups / e2e_s, unit=UNIT, seconds_per_step=e2e_s,
                  h2d_bytes_per_step=8 * p.M + 16 * p.M * p.M * 2, d2h_bytes_per_step=16 * p.M * p.M),
-        gpu_launches=int(r32["launches"]),
-        clocks=r32["clocks"],
+        gpu_launches=int(r32h["launches"]),
+        clocks=r32h["clocks"],
+        max_abs_vs_fp64_full=headline_vs_fp64,
         forms=forms,
-        rho_final=[[float(z.real), float(z.imag)] for z in r32["rho"].reshape(-1)],
+        rho_final=[[float(z.real), float(z.imag)] for z in r32h["rho"].reshape(-1)],
     )
     if rank == 0 and world == 1 and not args.no_cpu:
         nst = 2
