@@ -204,7 +204,7 @@ __device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*
 }
 
 template <int M, int FORM, int FPT>
-__global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs args) {
+__global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(BatchArgs args) {
     constexpr int M2 = M * M;
     using Elem = typename Form<FORM>::Elem;
     constexpr int TE = kBThreads * FPT;  // fibers (or growth entries) per tile
@@ -299,16 +299,48 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(BatchArgs args) {
                 const OpRef& op = (n == I.L) ? I.step_first : I.step;
                 const Elem* A = reinterpret_cast<const Elem*>(in);
                 Elem* out = reinterpret_cast<Elem*>(outv);
+                if constexpr (M == 2 && FORM == QUAPI_FP32 && FPT % 2 == 0) {
+                    // pairs of fibers: 64-byte aligned loads, 16-byte stores per row (F is even here)
 #pragma unroll
-                for (int u = 0; u < FPT; ++u) {
-                    const int64_t f = base + u;
-                    if (f < F) {
-                        Elem a[M2], o[M2];
+                    for (int u = 0; u < FPT; u += 2) {
+                        const int64_t f = base + u;
+                        if (f + 1 < F) {
+                            const float4* p4 = reinterpret_cast<const float4*>(A + f * M2);
+                            float4 v[4];
 #pragma unroll
-                        for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
-                        step_fiber_dispatch<M, FORM>(op, a, (uint32_t)f, o);
+                            for (int q = 0; q < 4; ++q) v[q] = __ldcg(p4 + q);
+                            Elem a0[M2] = {make_float2(v[0].x, v[0].y), make_float2(v[0].z, v[0].w),
+                                           make_float2(v[1].x, v[1].y), make_float2(v[1].z, v[1].w)};
+                            Elem a1[M2] = {make_float2(v[2].x, v[2].y), make_float2(v[2].z, v[2].w),
+                                           make_float2(v[3].x, v[3].y), make_float2(v[3].z, v[3].w)};
+                            Elem o0[M2], o1[M2];
+                            step_fiber_dispatch<M, FORM>(op, a0, (uint32_t)f, o0);
+                            step_fiber_dispatch<M, FORM>(op, a1, (uint32_t)(f + 1), o1);
 #pragma unroll
-                        for (int x = 0; x < M2; ++x) out[x * F + f] = o[x];
+                            for (int x = 0; x < M2; ++x)
+                                __stcg(reinterpret_cast<float4*>(out + x * F + f),
+                                       make_float4(o0[x].x, o0[x].y, o1[x].x, o1[x].y));
+                        } else if (f < F) {
+                            Elem a[M2], o[M2];
+#pragma unroll
+                            for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
+                            step_fiber_dispatch<M, FORM>(op, a, (uint32_t)f, o);
+#pragma unroll
+                            for (int x = 0; x < M2; ++x) out[x * F + f] = o[x];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < FPT; ++u) {
+                        const int64_t f = base + u;
+                        if (f < F) {
+                            Elem a[M2], o[M2];
+#pragma unroll
+                            for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
+                            step_fiber_dispatch<M, FORM>(op, a, (uint32_t)f, o);
+#pragma unroll
+                            for (int x = 0; x < M2; ++x) out[x * F + f] = o[x];
+                        }
                     }
                 }
             } else {
