@@ -323,7 +323,8 @@ def run_reference(args):
     line = dict(metric=METRIC, value=ups, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, sample=sample),
+                config=dict(workload=WORKLOAD, M=p.M, dkmax=p.L, N=p.N, form="fp64 oracle (CPU)", layout="full",
+                            readout="justFinalPoint", parallelism="replicas1", sample=sample),
                 cpu_baseline=dict(value=ups, unit=UNIT, cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=ups, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))

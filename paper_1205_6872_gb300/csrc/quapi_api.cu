@@ -236,6 +236,8 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
     return QUAPI_OK;
 }
 
+quapi_status tune_step(quapi_ctx* c);
+
 // Allocation, eta (given or by quadrature), propagators and tables.
 quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spectral* J, double beta,
                         const double* eta_host, double dt, int L, const quapi_opts* opts, quapi_ctx** out) {
@@ -393,6 +395,10 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     cudaFree(d_descs);
     if (d_jobs) cudaFree(d_jobs);
     if (d_gl) cudaFree(d_gl);
+    if (c->tune) {
+        quapi_status ts = tune_step(c);
+        if (ts != QUAPI_OK) return bail(ts);
+    }
 #undef SCHECK
     *out = c;
     return QUAPI_OK;
@@ -468,6 +474,64 @@ quapi_status run_point(quapi_ctx* c, int64_t n, const void* A_in, void* A_out, d
     if (!A_out) sp = nullptr;
     if (!sp && !rp) return QUAPI_OK;
     return run_step_op(c, sp, rp, A_in, A_out, rho_slot);
+}
+
+// Launch-shape autotuner for the steady-state step (quapi_opts.tune): times each
+// candidate (TMA staging with 2, 3 or 4 stages, or plain vector loads) on the
+// context's own buffers and keeps the fastest; results are cached per
+// (M, L, precision, layout) for the process.
+std::mutex g_tune_mutex;
+std::vector<std::pair<std::string, std::pair<int, int>>> g_tune_cache;
+
+quapi_status tune_step(quapi_ctx* c) {
+    if (c->M != 2 || c->herm || c->L < 6) return QUAPI_OK;  // a single kernel shape applies there
+    char keybuf[64];
+    std::snprintf(keybuf, sizeof(keybuf), "M%d L%d f%d", c->M, c->L, c->form);
+    const std::string key(keybuf);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (auto& kv : g_tune_cache)
+            if (kv.first == key) {
+                c->use_tma = kv.second.first != 0;
+                c->stages = kv.second.second;
+                return QUAPI_OK;
+            }
+    }
+    const int cand[4][2] = {{1, 2}, {1, 3}, {1, 4}, {0, 2}};
+    cudaEvent_t e0, e1;
+    QCHECK(c, cudaEventCreate(&e0), "event");
+    QCHECK(c, cudaEventCreate(&e1), "event");
+    float best = 1e30f;
+    int best_i = 0;
+    const int64_t n = c->L + 1;  // a steady-state step; the buffers' contents do not matter for timing
+    for (int i = 0; i < 4; ++i) {
+        c->use_tma = cand[i][0] != 0;
+        c->stages = cand[i][1];
+        quapi_status s = run_point(c, n, c->buf[0], c->buf[1], nullptr);
+        if (s != QUAPI_OK) break;
+        cudaEventRecord(e0, c->st);
+        for (int r = 0; r < 3; ++r) {
+            s = run_point(c, n, c->buf[r & 1], c->buf[(r & 1) ^ 1], nullptr);
+            if (s != QUAPI_OK) break;
+        }
+        cudaEventRecord(e1, c->st);
+        if (s != QUAPI_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->use_tma = cand[best_i][0] != 0;
+    c->stages = cand[best_i][1];
+    QCHECK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st), "clear error flag");
+    QCHECK(c, cudaStreamSynchronize(c->st), "tune synchronize");
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache.push_back({key, {cand[best_i][0], cand[best_i][1]}});
+    return QUAPI_OK;
 }
 
 quapi_status check_steps(quapi_ctx* c, const int64_t* steps, int nsteps) {

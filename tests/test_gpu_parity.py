@@ -255,6 +255,12 @@ def test_argument_errors(q):
         with pytest.raises(q.QuapiError) as e:
             q.quapi_propagate(ctx, pr["rho0"], [-1, 2], 2)
         assert e.value.status == q.QUAPI_ERR_ARG
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_propagate(ctx, pr["rho0"], [], 2)          # empty time grid
+        assert e.value.status == q.QUAPI_ERR_ARG
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_step_device(ctx, 0, 1, 1, None)             # no path point 0 step
+        assert e.value.status == q.QUAPI_ERR_ARG
     finally:
         q.quapi_destroy(ctx)
 
@@ -289,3 +295,19 @@ def test_checkpoint_resume_matches_uninterrupted(q, prec, tol):
         assert np.abs(got - want[k]).max() <= tol, k
     for got, k in zip(rest1, [40, 60]):
         assert np.abs(got - want[k]).max() <= tol, k
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5), (48, 1e-12)])
+def test_autotuned_step_matches_oracle(q, prec, tol):
+    """opts.tune picks the steady-step launch shape by timing; results must not change."""
+    pr = _problem(2, seed=5)
+    L, steps = 8, [0, 3, 8, 9, 40]
+    want = oracle.propagate(pr["s"], pr["H"], pr["spec"], pr["beta"], pr["dt"], L, pr["rho0"], steps)
+    ctx = q.quapi_setup(pr["s"], pr["H"], pr["spec"].kind, pr["spec"].a, pr["spec"].wc, pr["beta"], pr["dt"], L,
+                        q.quapi_opts_init(precision=prec, tune=1))
+    try:
+        got = q.quapi_propagate(ctx, pr["rho0"], steps, 2)
+    finally:
+        q.quapi_destroy(ctx)
+    for i, k in enumerate(steps):
+        assert np.abs(got[i] - want[k]).max() <= tol, k

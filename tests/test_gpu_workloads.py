@@ -152,3 +152,27 @@ def test_full_size_invariants_fp32(q):
     for r in got:
         assert abs(np.trace(r) - 1.0) < 1e-5
         assert np.abs(r - r.conj().T).max() < 1e-5
+
+
+def test_maximum_size_memory_length_16(q):
+    """dkmax = 16 (4^16 = 4.3 G entries, > 2^31): full layout FP32 (69 GB of tensors), half layout FP32
+    and half layout DF64 agree with each other and keep the trace and Hermiticity invariants."""
+    p = wl.spin_boson_L14()
+    L, steps = 16, [0, 5, 16, 17, 20]
+    res = {}
+    for name, prec, half in (("fp32_full", 32, 0), ("fp32_half", 32, 1), ("df64_half", 48, 1)):
+        ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, L,
+                            q.quapi_opts_init(precision=prec, hermitian=half))
+        try:
+            res[name] = q.quapi_propagate(ctx, p.rho0, steps, 2)
+        finally:
+            q.quapi_destroy(ctx)
+        torch.cuda.empty_cache()
+    for r in res["df64_half"]:
+        assert abs(np.trace(r) - 1.0) < 1e-12
+        assert np.abs(r - r.conj().T).max() < 1e-12
+    for name in ("fp32_full", "fp32_half"):
+        assert np.abs(res[name] - res["df64_half"]).max() < 1e-5, name
+    # the first steps stay within reach of the oracle's growth phase: check them exactly
+    want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, L, p.rho0, [5])[5]
+    assert np.abs(res["df64_half"][1] - want).max() < 1e-12
