@@ -36,16 +36,21 @@ template <> struct FormT<QUAPI_FP64> {
     using Elem = double2;
     using Tab = double2;
     static constexpr int FPT = 1;
+    // FP64 is bound by its FP64 pipe: the folded table lo (x) isum saves one complex product per row
+    static constexpr bool kFoldLo = true;
 };
 template <> struct FormT<QUAPI_FP32> {
     using Elem = float2;
     using Tab = ff2;
     static constexpr int FPT = 2;
+    // bound by memory: lo and isum stay separate (both staged in shared memory)
+    static constexpr bool kFoldLo = false;
 };
 template <> struct FormT<QUAPI_DF64> {
     using Elem = df2;
     using Tab = tf2;
     static constexpr int FPT = 1;
+    static constexpr bool kFoldLo = false;
 };
 
 template <int M> __device__ __forceinline__ constexpr bool is_diag(int x) { return (x / M) == (x % M); }
@@ -226,6 +231,7 @@ template <int M, int FORM> struct StepTables {
     static constexpr int M2 = M * M;
     Tab *isum, *isume, *lo, *loe;
     const Tab *hi, *hie;
+    const Tab *w, *we;  // lo (x) isum: [x][f_lo][old], read through L1
     uint32_t lo_size;
     int lo_shift;
     int64_t hi_size;
@@ -244,6 +250,8 @@ template <int M, int FORM> struct StepTables {
         loe = isume + M2 * M2;
         hi = reinterpret_cast<const Tab*>(args.hi);
         hie = reinterpret_cast<const Tab*>(args.hi_e);
+        w = reinterpret_cast<const Tab*>(args.w);
+        we = reinterpret_cast<const Tab*>(args.w_e);
         lo_size = (uint32_t)args.lo_size;
         lo_shift = args.lo_shift;
         hi_size = args.F / args.lo_size;
@@ -313,14 +321,27 @@ __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
                     vread[u] = apply_hi(same ? he0 : T.hie[hidx], Sd[u]);
                 }
             } else {
-                if (WRITE) {
-                    auto S = row_sum<M2>(T.isum + x * M2, a[u]);
-                    vout[u] = apply_p(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]], T.lo[x * T.lo_size + flo[u]], S);
-                }
-                if (READ) {
-                    auto Se = row_sum<M2>(T.isume + x * M2, a[u]);
-                    vread[u] = apply_p(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]],
-                                       T.loe[x * T.lo_size + flo[u]], Se);
+                if constexpr (FormT<FORM>::kFoldLo) {
+                    // w = lo (x) isum folds the lo factor into the sum over the oldest index
+                    if (WRITE) {
+                        auto S = row_sum<M2>(T.w + ((int64_t)x * T.lo_size + flo[u]) * M2, a[u]);
+                        vout[u] = apply_hi(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]], S);
+                    }
+                    if (READ) {
+                        auto Se = row_sum<M2>(T.we + ((int64_t)x * T.lo_size + flo[u]) * M2, a[u]);
+                        vread[u] = apply_hi(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]], Se);
+                    }
+                } else {
+                    if (WRITE) {
+                        auto S = row_sum<M2>(T.isum + x * M2, a[u]);
+                        vout[u] = apply_p(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]],
+                                          T.lo[x * T.lo_size + flo[u]], S);
+                    }
+                    if (READ) {
+                        auto Se = row_sum<M2>(T.isume + x * M2, a[u]);
+                        vread[u] = apply_p(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]],
+                                           T.loe[x * T.lo_size + flo[u]], Se);
+                    }
                 }
             }
             if (READ) racc[x].add(vread[u]);
@@ -683,19 +704,33 @@ template <int FORM, bool DIAG, bool END, bool ONLY1 = false>
 __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const typename FormT<FORM>::Elem (&a)[4],
                                           uint32_t f, typename FormT<FORM>::Elem (&o)[4]) {
     const uint32_t fh = f >> T.lo_shift, fl = f & (T.lo_size - 1u);
-    const auto* isum = END ? T.isume : T.isum;
-    const auto* lo = END ? T.loe : T.lo;
     const auto* hi = END ? T.hie : T.hi;
-    if (ONLY1) {
-    } else if (DIAG) {
-        const auto S = plain_sum<4>(a);
-        o[0] = apply_hi(hi[fh], S);
-        o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
+    if constexpr (FormT<FORM>::kFoldLo) {
+        const auto* w = END ? T.we : T.w;  // lo (x) isum
+        if (ONLY1) {
+        } else if (DIAG) {
+            const auto S = plain_sum<4>(a);
+            o[0] = apply_hi(hi[fh], S);
+            o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
+        } else {
+            o[0] = apply_hi(hi[fh], row_sum<4>(w + (int64_t)fl * 4, a));
+            o[3] = apply_hi(hi[3 * T.hi_size + fh], row_sum<4>(w + ((int64_t)3 * T.lo_size + fl) * 4, a));
+        }
+        o[1] = apply_hi(hi[T.hi_size + fh], row_sum<4>(w + ((int64_t)T.lo_size + fl) * 4, a));
     } else {
-        o[0] = apply_p(hi[fh], lo[fl], row_sum<4>(isum, a));
-        o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4>(isum + 12, a));
+        const auto* isum = END ? T.isume : T.isum;
+        const auto* lo = END ? T.loe : T.lo;
+        if (ONLY1) {
+        } else if (DIAG) {
+            const auto S = plain_sum<4>(a);
+            o[0] = apply_hi(hi[fh], S);
+            o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
+        } else {
+            o[0] = apply_p(hi[fh], lo[fl], row_sum<4>(isum, a));
+            o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4>(isum + 12, a));
+        }
+        o[1] = apply_p(hi[T.hi_size + fh], lo[T.lo_size + fl], row_sum<4>(isum + 4, a));
     }
-    o[1] = apply_p(hi[T.hi_size + fh], lo[T.lo_size + fl], row_sum<4>(isum + 4, a));
 }
 
 template <int FORM, bool WRITE, bool READ, bool DIAG>

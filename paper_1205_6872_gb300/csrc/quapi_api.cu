@@ -176,6 +176,9 @@ void assign_offsets(OpPlan& p, int M2, int form, size_t& cursor) {
     cursor = align(cursor);
     p.off_hi = cursor;
     cursor += (size_t)M2 * p.hi_size * e;
+    cursor = align(cursor);
+    p.off_w = cursor;
+    if (p.summed) cursor += (size_t)M2 * p.lo_size * M2 * e;
 }
 
 // every table set the context needs, in a fixed order
@@ -383,7 +386,8 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         d.isum = c->d_tables + p.off_isum;
         d.lo = c->d_tables + p.off_lo;
         d.hi = c->d_tables + p.off_hi;
-        int64_t ent = (p.summed ? M2 * M2 : 0) + M2 * p.lo_size + M2 * p.hi_size;
+        d.w = c->d_tables + p.off_w;
+        int64_t ent = (p.summed ? M2 * M2 + M2 * p.lo_size * M2 : 0) + M2 * p.lo_size + M2 * p.hi_size;
         max_entries = std::max(max_entries, ent);
     }
     BuildDesc* d_descs = nullptr;
@@ -418,11 +422,13 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
         a.isum = c->d_tables + sp->off_isum;
         a.lo = c->d_tables + sp->off_lo;
         a.hi = c->d_tables + sp->off_hi;
+        a.w = c->d_tables + sp->off_w;
     }
     if (rp) {
         a.isum_e = c->d_tables + rp->off_isum;
         a.lo_e = c->d_tables + rp->off_lo;
         a.hi_e = c->d_tables + rp->off_hi;
+        a.w_e = c->d_tables + rp->off_w;
         a.partial = c->d_partial;
     }
     a.lo_size = ref->lo_size;
@@ -631,6 +637,7 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     a->isum_e = c->d_tables + rp->off_isum;
     a->lo_e = c->d_tables + rp->off_lo;
     a->hi_e = c->d_tables + rp->off_hi;
+    a->w_e = c->d_tables + rp->off_w;
     a->lo_size = rp->lo_size;
     int sh = 0;
     while ((int64_t(1) << sh) < rp->lo_size) ++sh;

@@ -173,6 +173,7 @@ struct OpPlan {
     int eta_idx[kMaxDigits] = {0};  // eta index (into the 4L+3 vector) per input digit
     int self_idx = 0;    // eta index of the new point's self term
     size_t off_isum = 0, off_lo = 0, off_hi = 0;  // byte offsets in the table arena
+    size_t off_w = 0;    // summed ops: w[x][f_lo][old] = lo[x][f_lo] * isum[x][old]
 };
 
 // Device-side build request for one OpPlan (all pointers device).
@@ -187,6 +188,7 @@ struct BuildDesc {
     void* isum;
     void* lo;
     void* hi;
+    void* w;              // summed ops: lo (x) isum, M2 x lo_size x M2 entries
 };
 
 // eta quadrature request: one integral per entry.
@@ -217,6 +219,8 @@ struct StepArgs {
     const void* isum_e;   // readout tables (null if no readout)
     const void* lo_e;
     const void* hi_e;
+    const void* w;        // lo (x) isum of the step, [x][f_lo][old]
+    const void* w_e;      // the same for the readout
     int64_t lo_size;      // (M^2)^j, common to step and readout tables
     int lo_shift;         // log2(lo_size) when M = 2
     double2* partial;     // [grid][M^2] readout partial sums

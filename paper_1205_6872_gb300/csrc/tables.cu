@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(kBuildThreads) build_tables_kernel(const Build
     const int64_t n_isum = D.summed ? (int64_t)M2 * M2 : 0;
     const int64_t n_lo = (int64_t)M2 * D.lo_size;
     const int64_t n_hi = (int64_t)M2 * D.hi_size;
-    const int64_t total = n_isum + n_lo + n_hi;
+    const int64_t n_w = D.summed ? (int64_t)M2 * D.lo_size * M2 : 0;
+    const int64_t total = n_isum + n_lo + n_hi + n_w;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         if (e < n_isum) {
@@ -190,6 +191,20 @@ __global__ void __launch_bounds__(kBuildThreads) build_tables_kernel(const Build
                 v = cmul(v, G[D.summed + t][x][digit]);
             }
             store_entry(D.lo, q, D.form, v);
+        } else if (e >= n_isum + n_lo + n_hi) {
+            // w[x][f_lo][old] = (prod over the lo digits of G)(x, f_lo) * G_0(x, old)
+            const int64_t q = e - n_isum - n_lo - n_hi;
+            const int x = (int)(q / (D.lo_size * M2));
+            const int64_t rem = q % (D.lo_size * M2);
+            int64_t i = rem / M2;
+            const int old = (int)(rem % M2);
+            double2 v = G[0][x][old];
+            for (int t = 0; t < D.j; ++t) {
+                int digit = (int)(i % M2);
+                i /= M2;
+                v = cmul(v, G[D.summed + t][x][digit]);
+            }
+            store_entry(D.w, q, D.form, v);
         } else {
             int64_t q = e - n_isum - n_lo;
             int x = (int)(q / D.hi_size);
