@@ -638,6 +638,41 @@ __device__ __forceinline__ void half_decode(uint32_t c, int n, uint32_t& plain, 
     sc = true;
 }
 
+// half_decode together with the prefix fh = f >> 2 (f without its last digit,
+// n - 1 digits): its canonical position h and whether it is its own conjugate.
+// The digits above f's first digit 1 are shared with fh, so one walk down the
+// levels gives both positions (fh of a canonical f is canonical).
+__device__ __forceinline__ void half_decode_pair(uint32_t c, int n, uint32_t& plain, bool& sc, uint32_t& h,
+                                                 bool& shc) {
+    uint32_t p = 0, hoff = 0;
+    for (int level = n; level >= 1; --level) {
+        const uint32_t r1 = 1u << (2 * (level - 1));
+        if (c < r1) {  // digit 1 at this level, the rest is plain
+            plain = (p << (2 * level)) | r1 | c;
+            sc = false;
+            h = hoff + (c >> 2);      // level >= 2: fh keeps the digit 1 and the plain rest c >> 2
+            shc = (level == 1);       // level 1: the digit 1 was f's last digit, fh is all 0s and 3s
+            return;
+        }
+        c -= r1;
+        const uint32_t cn1 = half_count32(level - 1);
+        // fh's layout at level - 1: [digit 1: r1 / 4][digit 0: C(level - 2)][digit 3: C(level - 2)]
+        const uint32_t skip = (level >= 2) ? (r1 >> 2) : 0u;
+        if (c < cn1) {
+            p = p << 2;
+            hoff += skip;
+        } else {
+            c -= cn1;
+            p = (p << 2) | 3u;
+            hoff += (level >= 2) ? skip + half_count32(level - 2) : 0u;
+        }
+    }
+    plain = p;
+    sc = true;
+    h = hoff;
+    shc = true;
+}
+
 // canonical position of a canonical n-digit prefix given by its plain digits
 __device__ __forceinline__ uint32_t half_position(uint32_t h, int n) {
     uint32_t idx = 0;
@@ -733,10 +768,83 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
     }
 }
 
+// Everything one canonical input prefix f contributes: its decoded plain digits f, whether f is its
+// own conjugate (sc), the canonical position h of fh = f >> 2 and whether fh is its own conjugate (shc).
+// The store position h (and shc) is found after the rows are computed, which keeps it out of the
+// arithmetic's live range: given (hfast, shc = false) when known, else decoded from f.
 template <int FORM, bool WRITE, bool READ, bool DIAG>
-__global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
+__device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const typename FormT<FORM>::Elem (&a)[4],
+                                           uint32_t f, bool sc, bool known, uint32_t hfast, int np, uint32_t top,
+                                           uint32_t cnh, typename FormT<FORM>::Elem* __restrict__ out,
+                                           RhoAcc<FORM> (&racc)[4]) {
     using Elem = typename FormT<FORM>::Elem;
-    constexpr int U = 1;  // prefixes per thread per iteration
+    constexpr int remap[4] = {0, 2, 1, 3};
+    Elem b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = conjv(a[remap[q]]);  // fiber of the conjugate prefix
+    const uint32_t fb = conj_digits(f);
+    if (WRITE) {
+        Elem o[4];
+        herm_rows<FORM, DIAG, false>(T, a, f, o);
+        if (np == 0) {  // one-digit output: every point stored
+            st_stream(out + 0, o[0]);
+            st_stream(out + 1, o[1]);
+            st_stream(out + 2, conjv(o[1]));
+            st_stream(out + 3, o[3]);
+        } else {
+            const uint32_t fl = f & 3u;
+            const uint32_t h = known ? hfast : half_position(f >> 2, np - 1);
+            const bool shc = known ? false : self_conjugate(f >> 2, np - 1);
+            const uint32_t b0 = 4u * (top + h), b3 = 4u * (top + cnh + h);
+            st_stream(out + f, o[1]);
+            st_stream(out + b0 + fl, o[0]);
+            st_stream(out + b3 + fl, o[3]);
+            if (!sc) {
+                Elem ob[4];
+                herm_rows<FORM, DIAG, false, true>(T, b, fb, ob);
+                st_stream(out + fb, ob[1]);
+                if (shc) {  // (0/3, fh, 2) are stored too: conjugates of (0/3, f)
+                    st_stream(out + b0 + 2, conjv(o[0]));
+                    st_stream(out + b3 + 2, conjv(o[3]));
+                }
+            }
+        }
+    }
+    if (READ) {
+        Elem r[4];
+        herm_rows<FORM, DIAG, true>(T, a, f, r);
+        racc[1].add(r[1]);
+        if (!sc) {
+            Elem rb[4];
+            herm_rows<FORM, DIAG, true, true>(T, b, fb, rb);
+            racc[1].add(rb[1]);
+            racc[0].add(twice_real(r[0]));
+            racc[3].add(twice_real(r[3]));
+        } else {
+            racc[0].add(real_part(r[0]));
+            racc[3].add(real_part(r[3]));
+        }
+    }
+}
+
+// Work is handed out in warp chunks of kChunk consecutive canonical positions (kChunk / 32 per lane).
+// Nearly every chunk lies inside one digit-1 block of level >= 2 (all but the last few levels):
+// it is decoded once and its prefixes are then consecutive plain indices, f = f0 + i with fiber
+// position h = h0 + i / 4.  Other chunks decode each position on its own.
+constexpr uint32_t kChunk = 256;
+
+// Minimum resident CTAs per SM given to the compiler (a register cap).  Measured at memory length 14:
+// the FP32 step runs best at 6 CTAs (40 registers, no spills); kernels with the readout, and the
+// DF64 and FP64 forms, at 3-4.
+template <int FORM, bool WRITE, bool READ> constexpr int herm_min_ctas() {
+    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 6 : 4;
+    if (WRITE && READ) return 3;
+    return (FORM == QUAPI_DF64 && READ) ? 3 : 4;
+}
+
+template <int FORM, bool WRITE, bool READ, bool DIAG>
+__global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) herm_step_kernel(StepArgs args) {
+    using Elem = typename FormT<FORM>::Elem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepTables<2, FORM> T;
     T.template stage<WRITE, READ>(args, smem_raw);
@@ -750,64 +858,34 @@ __global__ void __launch_bounds__(kThreads) herm_step_kernel(StepArgs args) {
     const uint32_t npre = half_count32(np);
     const uint32_t top = (np >= 1) ? (1u << (2 * (np - 1))) : 0u;   // 4^(np-1)
     const uint32_t cnh = (np >= 1) ? half_count32(np - 1) : 0u;
-    constexpr int remap[4] = {0, 2, 1, 3};
-    for (uint32_t c0 = (blockIdx.x * kThreads + threadIdx.x) * U; c0 < npre; c0 += gridDim.x * kThreads * U) {
-        Elem a[U][4];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (c0 + u < npre) load_fiber4<FORM>(A, c0 + u, a[u]);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t c = c0 + u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nwarps = gridDim.x * (kThreads / 32);
+#pragma unroll 1
+    for (uint32_t cb = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * kChunk; cb < npre;
+         cb += nwarps * kChunk) {
+        uint32_t fb0, hb0;
+        bool sc0, shc0;
+        half_decode_pair(cb, np, fb0, sc0, hb0, shc0);
+        // r1 = 4^(level - 1) of the chunk's digit-1 block (the lowest bit of f's top digit outside {0, 3});
+        // the chunk stays inside it when fb0's offset in the block + kChunk <= r1 (fb0 a multiple of 4)
+        const uint32_t t = (fb0 ^ (fb0 >> 1)) & 0x55555555u;
+        const uint32_t r1 = t ? (1u << (31 - __clz(t))) : 0u;
+        const bool fast = !sc0 && !shc0 && (fb0 & 3u) == 0u && (fb0 & (r1 - 1u)) + kChunk <= r1;
+#pragma unroll 1
+        for (uint32_t i = lane; i < kChunk; i += 32) {
+            const uint32_t c = cb + i;
             if (c >= npre) break;
+            Elem a[4];
+            load_fiber4<FORM>(A, c, a);
             uint32_t f;
             bool sc;
-            half_decode(c, np, f, sc);
-            Elem b[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) b[q] = conjv(a[u][remap[q]]);  // fiber of the conjugate prefix
-            const uint32_t fb = conj_digits(f);
-            if (WRITE) {
-                Elem o[4];
-                herm_rows<FORM, DIAG, false>(T, a[u], f, o);
-                if (np == 0) {  // one-digit output: every point stored
-                    st_stream(out + 0, o[0]);
-                    st_stream(out + 1, o[1]);
-                    st_stream(out + 2, conjv(o[1]));
-                    st_stream(out + 3, o[3]);
-                } else {
-                    const uint32_t fl = f & 3u, fh = f >> 2;
-                    const uint32_t h = half_position(fh, np - 1);
-                    const uint32_t b0 = 4u * (top + h), b3 = 4u * (top + cnh + h);
-                    st_stream(out + f, o[1]);
-                    st_stream(out + b0 + fl, o[0]);
-                    st_stream(out + b3 + fl, o[3]);
-                    if (!sc) {
-                        Elem ob[4];
-                        herm_rows<FORM, DIAG, false, true>(T, b, fb, ob);
-                        st_stream(out + fb, ob[1]);
-                        if (self_conjugate(fh, np - 1)) {  // (0/3, fh, 2) are stored too: conjugates of (0/3, f)
-                            st_stream(out + b0 + 2, conjv(o[0]));
-                            st_stream(out + b3 + 2, conjv(o[3]));
-                        }
-                    }
-                }
+            if (fast) {
+                f = fb0 + i;
+                sc = false;
+            } else {
+                half_decode(c, np, f, sc);
             }
-            if (READ) {
-                Elem r[4];
-                herm_rows<FORM, DIAG, true>(T, a[u], f, r);
-                racc[1].add(r[1]);
-                if (!sc) {
-                    Elem rb[4];
-                    herm_rows<FORM, DIAG, true, true>(T, b, fb, rb);
-                    racc[1].add(rb[1]);
-                    racc[0].add(twice_real(r[0]));
-                    racc[3].add(twice_real(r[3]));
-                } else {
-                    racc[0].add(real_part(r[0]));
-                    racc[3].add(real_part(r[3]));
-                }
-            }
+            herm_fiber<FORM, WRITE, READ, DIAG>(T, a, f, sc, fast, hb0 + (i >> 2), np, top, cnh, out, racc);
         }
     }
     if (READ) {
@@ -1062,8 +1140,7 @@ cudaError_t launch_herm_variant(StepArgs& a, cudaStream_t st) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
-    const int U = 1;
-    const int64_t work = (half_count(a.half_digits) + (int64_t)kThreads * U - 1) / ((int64_t)kThreads * U);
+    const int64_t work = (half_count(a.half_digits) + kThreads - 1) / kThreads;
     int64_t g = (int64_t)num_sms() * (occ < 1 ? 1 : occ);
     if (g > work) g = work;
     if (g > a.grid) g = a.grid;
