@@ -834,10 +834,10 @@ __device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const t
 constexpr uint32_t kChunk = 256;
 
 // Minimum resident CTAs per SM given to the compiler (a register cap).  Measured at memory length 14:
-// the FP32 step runs best at 6 CTAs (40 registers, no spills); kernels with the readout, and the
-// DF64 and FP64 forms, at 3-4.
+// the FP32 step runs best at 8 CTAs (32 registers; 0.370 ms against 0.380 ms at 6 CTAs and
+// 0.425 ms uncapped); kernels with the readout, and the DF64 and FP64 forms, at 3-4.
 template <int FORM, bool WRITE, bool READ> constexpr int herm_min_ctas() {
-    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 6 : 4;
+    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 8 : 4;
     if (WRITE && READ) return 3;
     return (FORM == QUAPI_DF64 && READ) ? 3 : 4;
 }
