@@ -240,31 +240,34 @@ def batch_updates(probs):
 
 
 def time_batched(q, torch, steps, warmup, world, rank):
-    """256 spin-boson instances: one batched FP32 launch (autotuned, graph replay) vs the
-    same instances solved one after another with the plain FP64 propagator.  Under N ranks
-    each rank takes a contiguous shard of the instances."""
+    """256 spin-boson instances: one batched FP32 launch (autotuned, graph replay), with the tiled
+    instances in the Hermitian half layout and in the full layout, vs the same instances solved one
+    after another with the plain FP64 propagator.  Under N ranks each rank takes a contiguous shard
+    of the instances."""
     from paper_1205_6872_gb300 import replicas
     from paper_1205_6872_gb300 import workloads as wl
     allp = wl.batched_256()
     a, b = replicas.shard(len(allp), rank, world)
     probs = allp[a:b]
     ups = batch_updates(probs)
-    c32 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
-                         q.quapi_opts_init(precision=q.QUAPI_FP32, tune=1)) for p in probs]
-    try:
-        rho0s = [p.rho0 for p in probs]
-        Ns = [p.N for p in probs]
-        for _ in range(max(warmup, 1)):
-            q.quapi_propagate_batch(c32, rho0s, Ns)  # first call tunes and captures the graph
-        torch.cuda.synchronize()
-        replicas.barrier()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            r32 = q.quapi_propagate_batch(c32, rho0s, Ns)
-        batched_s = replicas.reduce_max((time.perf_counter() - t0) / steps)
-    finally:
-        for c in c32:
-            q.quapi_destroy(c)
+    rho0s = [p.rho0 for p in probs]
+    Ns = [p.N for p in probs]
+    batched_s, r32 = {}, {}
+    for half in (1, 0):
+        c32 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                             q.quapi_opts_init(precision=q.QUAPI_FP32, tune=1, hermitian=half)) for p in probs]
+        try:
+            for _ in range(max(warmup, 1)):
+                q.quapi_propagate_batch(c32, rho0s, Ns)  # first call tunes and captures the graph
+            torch.cuda.synchronize()
+            replicas.barrier()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                r32[half] = q.quapi_propagate_batch(c32, rho0s, Ns)
+            batched_s[half] = replicas.reduce_max((time.perf_counter() - t0) / steps)
+        finally:
+            for c in c32:
+                q.quapi_destroy(c)
     c64 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
                          q.quapi_opts_init(precision=q.QUAPI_FP64)) for p in probs]
     try:
@@ -282,12 +285,14 @@ def time_batched(q, torch, steps, warmup, world, rank):
     finally:
         for c in c64:
             q.quapi_destroy(c)
-    diff = replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32, r64)))
+    diff = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32[h], r64))) for h in (0, 1)}
     total = replicas.reduce_sum(ups)
-    return dict(workload="batched_256", instances=len(allp), value=total / batched_s, unit=UNIT,
-                ms_per_batch=1000.0 * batched_s, sequential_fp64_ms=1000.0 * seq_s,
-                sequential_fp64_value=total / seq_s, speedup_vs_sequential_fp64=seq_s / batched_s,
-                fp32_vs_fp64_max_abs=diff)
+    return dict(workload="batched_256", instances=len(allp), layout="half (tiled instances)",
+                value=total / batched_s[1], unit=UNIT, ms_per_batch=1000.0 * batched_s[1],
+                full_layout_value=total / batched_s[0], full_layout_ms_per_batch=1000.0 * batched_s[0],
+                sequential_fp64_ms=1000.0 * seq_s, sequential_fp64_value=total / seq_s,
+                speedup_vs_sequential_fp64=seq_s / batched_s[1], fp32_vs_fp64_max_abs=diff[1],
+                fp32_full_vs_fp64_max_abs=diff[0])
 
 
 def cpu_oracle_sample(p, nsteps):
@@ -379,14 +384,15 @@ def run_kernel_only(args):
 
 def run_batched_only(args):
     """One batched FP32 launch over --batch-n seeded spin-boson instances (3 warm-up runs, then
-    --reps timed runs).  Used for ncu captures of the batched kernel on a small case."""
+    --reps timed runs), optionally in the half layout and autotuned.  Used for ncu captures of the
+    batched kernel on a small case."""
     import torch
     from paper_1205_6872_gb300 import quapi as q
     from paper_1205_6872_gb300 import workloads as wl
     torch.cuda.set_device(0)
     probs = wl.batched_256(n=args.batch_n, N=args.batch_steps)
-    ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
-                          q.quapi_opts_init(precision=q.QUAPI_FP32)) for p in probs]
+    opts = q.quapi_opts_init(precision=q.QUAPI_FP32, tune=int(args.tune), hermitian=int(args.hermitian))
+    ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, opts) for p in probs]
     try:
         rho0s, Ns = [p.rho0 for p in probs], [p.N for p in probs]
         for _ in range(3):
@@ -399,7 +405,8 @@ def run_batched_only(args):
     finally:
         for c in ctxs:
             q.quapi_destroy(c)
-    print(json.dumps(dict(mode="batched-only", instances=len(probs), N=args.batch_steps, ms_per_batch=ms,
+    print(json.dumps(dict(mode="batched-only", instances=len(probs), N=args.batch_steps, hermitian=bool(args.hermitian),
+                          tune=bool(args.tune), ms_per_batch=ms,
                           value=batch_updates(probs) / (ms / 1e3), unit=UNIT)))
     return 0
 
@@ -418,7 +425,8 @@ def main():
     ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
     ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"], help="form for --kernel-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
-    ap.add_argument("--hermitian", action="store_true", help="--kernel-only: Hermitian half layout")
+    ap.add_argument("--hermitian", action="store_true", help="--kernel-only / --batched-only: Hermitian half layout")
+    ap.add_argument("--tune", action="store_true", help="--batched-only: autotune the launch shape")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the batched launch on a seeded batch (profiling case)")
     ap.add_argument("--batch-n", type=int, default=256, help="instances for --batched-only")

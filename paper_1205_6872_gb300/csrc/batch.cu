@@ -29,6 +29,7 @@
 #include <string>
 #include <vector>
 
+#include "half_layout.cuh"
 #include "step_math.cuh"
 
 namespace quapi {
@@ -143,6 +144,196 @@ __device__ void step_fiber_dispatch(const OpRef& op, const typename Form<FORM>::
         fiber_step<M, FORM, true>(T, a, f, o);
     else
         fiber_step<M, FORM, false>(T, a, f, o);
+}
+
+// ---- Hermitian half layout (M = 2) for tiled instances ----------------------------
+// Positions, rows and conjugate partners as in the single-instance half-layout kernels: one
+// canonical prefix gives rows 1, 0 and 3 of its fiber and row 1 of its conjugate prefix.
+
+template <int FORM> __device__ __forceinline__ void ld_fiber4(const typename Form<FORM>::Elem* A, uint32_t c,
+                                                             typename Form<FORM>::Elem (&a)[4]) {
+    if constexpr (FORM == QUAPI_FP32) {
+        const float4* p = reinterpret_cast<const float4*>(A + 4ull * c);
+        const float4 v0 = __ldcg(p), v1 = __ldcg(p + 1);
+        a[0] = make_float2(v0.x, v0.y);
+        a[1] = make_float2(v0.z, v0.w);
+        a[2] = make_float2(v1.x, v1.y);
+        a[3] = make_float2(v1.z, v1.w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = ld_l2(A + 4ull * c + q);
+    }
+}
+
+// rows 0, 1, 3 of fiber a at prefix f (ONLY1: row 1 alone); the diagonal rows use the plain sum when
+// the operation allows it
+template <int FORM, bool ONLY1>
+__device__ __forceinline__ void herm_rows_b(const OpTabs<2, FORM>& T, bool diag,
+                                            const typename Form<FORM>::Elem (&a)[4], uint32_t f,
+                                            typename Form<FORM>::Elem (&o)[4]) {
+    using Elem = typename Form<FORM>::Elem;
+    uint32_t fh, fl;
+    T.split(f, fh, fl);
+    if (!ONLY1) {
+        if (diag) {
+            Elem c;
+            const Elem s = plain_dot<4>(a, c);
+            o[0] = tab_mul2(ldt(T.hi + fh), s, c);
+            o[3] = tab_mul2(ldt(T.hi + 3 * T.hi_size + fh), s, c);
+        } else {
+#pragma unroll
+            for (int x = 0; x < 4; x += 3) {
+                Elem c;
+                const Elem s = tab_dot<4>(T.isum + x * 4, a, c);
+                o[x] = tab_mul(ldt(T.hi + (int64_t)x * T.hi_size + fh), tab_mul2(ldt(T.lo + x * T.lo_size + fl), s, c));
+            }
+        }
+    }
+    Elem c;
+    const Elem s = tab_dot<4>(T.isum + 4, a, c);
+    o[1] = tab_mul(ldt(T.hi + T.hi_size + fh), tab_mul2(ldt(T.lo + T.lo_size + fl), s, c));
+}
+
+// Decode of position c (np digits) for one lane of a warp whose 32 lanes take the consecutive
+// positions c0 .. c0 + 31 (c = c0 + lane): when the 32 stay in one digit-1 block of level >= 2 the
+// warp decodes c0 once, otherwise each lane decodes its own position.
+__device__ __forceinline__ void herm_decode_warp(uint32_t c0, uint32_t lane, int np, uint32_t& f, bool& sc,
+                                                 uint32_t& h, bool& shc) {
+    uint32_t f0, h0;
+    bool sc0, shc0;
+    half_decode_pair(c0, np, f0, sc0, h0, shc0);
+    const uint32_t t = (f0 ^ (f0 >> 1)) & 0x55555555u;
+    const uint32_t r1 = t ? (1u << (31 - __clz(t))) : 0u;
+    if (!sc0 && !shc0 && (f0 & 3u) == 0u && (f0 & (r1 - 1u)) + 32u <= r1) {
+        f = f0 + lane;
+        h = h0 + (lane >> 2);
+        sc = false;
+        shc = false;
+    } else {
+        half_decode_pair(c0 + lane, np, f, sc, h, shc);
+    }
+}
+
+// Steady step: positions c = base + u * kBThreads + threadIdx.x of the np-digit canonical prefixes.
+template <int FORM, int FPT>
+__device__ void herm_step_tile(const OpRef& op, const void* in, void* outv, int np, int64_t tile_base) {
+    using Elem = typename Form<FORM>::Elem;
+    constexpr int remap[4] = {0, 2, 1, 3};
+    const OpTabs<2, FORM> T = tabs_of<2, FORM>(op);
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    Elem* out = reinterpret_cast<Elem*>(outv);
+    const uint32_t npre = half_count32(np);
+    const uint32_t top = (np >= 1) ? (1u << (2 * (np - 1))) : 0u;
+    const uint32_t cnh = (np >= 1) ? half_count32(np - 1) : 0u;
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t c0 = (uint32_t)tile_base + u * kBThreads + (threadIdx.x & ~31u);
+        if (c0 >= npre) break;
+        const uint32_t c = c0 + lane;
+        uint32_t f = 0, h = 0;
+        bool sc = true, shc = true;
+        herm_decode_warp(c0, lane, np, f, sc, h, shc);  // warp-uniform call: every lane takes part
+        if (c >= npre) continue;
+        Elem a[4], o[4];
+        ld_fiber4<FORM>(A, c, a);
+        herm_rows_b<FORM, false>(T, op.diag != 0, a, f, o);
+        if (np == 0) {
+            out[0] = o[0];
+            out[1] = o[1];
+            out[2] = conjv(o[1]);
+            out[3] = o[3];
+            continue;
+        }
+        const uint32_t b0 = 4u * (top + h), b3 = 4u * (top + cnh + h), fl = f & 3u;
+        out[f] = o[1];
+        out[b0 + fl] = o[0];
+        out[b3 + fl] = o[3];
+        if (!sc) {
+            Elem b[4], ob[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = conjv(a[remap[q]]);
+            const uint32_t fb = conj_digits(f);
+            herm_rows_b<FORM, true>(T, op.diag != 0, b, fb, ob);
+            out[fb] = ob[1];
+            if (shc) {
+                out[b0 + 2] = conjv(o[0]);
+                out[b3 + 2] = conjv(o[3]);
+            }
+        }
+    }
+}
+
+// Readout contributions of positions c = base + u * kBThreads + threadIdx.x (np-digit prefixes):
+// row 1 over f and its conjugate, twice the real part of rows 0 and 3 (their partners are conjugates);
+// row 2 of rho is the conjugate of row 1 and is filled in by the caller.
+template <int FORM, int FPT>
+__device__ void herm_read_tile(const OpRef& op, const void* in, int np, int64_t tile_base, Acc<FORM> (&acc)[4]) {
+    using Elem = typename Form<FORM>::Elem;
+    constexpr int remap[4] = {0, 2, 1, 3};
+    const OpTabs<2, FORM> T = tabs_of<2, FORM>(op);
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    const uint32_t npre = half_count32(np);
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t c = (uint32_t)tile_base + u * kBThreads + threadIdx.x;
+        if (c >= npre) break;
+        uint32_t f;
+        bool sc;
+        half_decode(c, np, f, sc);
+        Elem a[4], r[4];
+        ld_fiber4<FORM>(A, c, a);
+        herm_rows_b<FORM, false>(T, op.diag != 0, a, f, r);
+        acc[1].add(r[1]);
+        if (!sc) {
+            Elem b[4], rb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = conjv(a[remap[q]]);
+            herm_rows_b<FORM, true>(T, op.diag != 0, b, conj_digits(f), rb);
+            acc[1].add(rb[1]);
+            acc[0].add(twice_real(r[0]));
+            acc[3].add(twice_real(r[3]));
+        } else {
+            acc[0].add(real_part(r[0]));
+            acc[3].add(real_part(r[3]));
+        }
+    }
+}
+
+// Growth n_in -> n_in + 1 digits: stored input entries e = base + u * kBThreads + threadIdx.x.
+template <int FORM, int FPT>
+__device__ void herm_grow_tile(const OpRef& op, const void* in, void* outv, int n_in, int64_t tile_base) {
+    using Elem = typename Form<FORM>::Elem;
+    const OpTabs<2, FORM> T = tabs_of<2, FORM>(op);
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    Elem* out = reinterpret_cast<Elem*>(outv);
+    const uint32_t S = 1u << (2 * n_in);          // plain row-1 block of the output
+    const uint32_t Cp = half_count32(n_in - 1);  // canonical prefixes of the input
+    auto Pm = [&](int x, uint32_t idx, Elem w) {
+        uint32_t ih, il;
+        T.split(idx, ih, il);
+        return tab_mul(ldt(T.hi + (int64_t)x * T.hi_size + ih), tab_mul(ldt(T.lo + x * T.lo_size + il), w));
+    };
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t e = (uint32_t)tile_base + u * kBThreads + threadIdx.x;
+        if (e >= 4u * Cp) break;
+        const uint32_t c = e >> 2, d = e & 3u;
+        uint32_t P;
+        bool scP;
+        half_decode(c, n_in - 1, P, scP);
+        const uint32_t i = (P << 2) | d;
+        const Elem v = ld_l2(A + e);
+        if (!(scP && d == 2u)) {  // (P, 2) of a self-conjugate P is written from (P, 1)
+            out[i] = Pm(1, i, v);
+            if (!(scP && (d == 0u || d == 3u))) {
+                const uint32_t ib = conj_digits(i);
+                out[ib] = Pm(1, ib, conjv(v));
+            }
+        }
+        out[4u * ((S >> 2) + c) + d] = Pm(0, i, v);
+        out[4u * ((S >> 2) + Cp + c) + d] = Pm(3, i, v);
+    }
 }
 
 // One instance, every step in shared memory (resident instances).
@@ -277,7 +468,13 @@ __global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(Batc
         void* outv = I.buf[n & 1];
         for (unsigned t = t0; t < t1; ++t) {
             const int64_t base = (int64_t)t * TE + (int64_t)threadIdx.x * FPT;
-            if (n < I.L && n < I.N) {
+            const bool herm = (M == 2) && I.herm;
+            if (herm && n < I.N) {
+                if constexpr (M == 2) {
+                    if (n < I.L) herm_grow_tile<FORM, FPT>(I.grow[n], in, outv, n, (int64_t)t * TE);
+                    else herm_step_tile<FORM, FPT>(n == I.L ? I.step_first : I.step, in, outv, I.L - 1, (int64_t)t * TE);
+                }
+            } else if (n < I.L && n < I.N) {
                 int64_t S = 1;
                 for (int i = 0; i < n; ++i) S *= M2;
                 const OpTabs<M, FORM> T = tabs_of<M, FORM>(I.grow[n]);
@@ -350,20 +547,28 @@ __global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(Batc
                 Acc<FORM> acc[M2];
 #pragma unroll
                 for (int x = 0; x < M2; ++x) acc[x].init();
+                if (herm) {
+                    if constexpr (M == 2) herm_read_tile<FORM, FPT>(I.read, in, I.read.n_in - 1, (int64_t)t * TE, acc);
+                } else {
 #pragma unroll
-                for (int u = 0; u < FPT; ++u) {
-                    const int64_t f = base + u;
-                    if (f < F) {
-                        Elem a[M2], o[M2];
+                    for (int u = 0; u < FPT; ++u) {
+                        const int64_t f = base + u;
+                        if (f < F) {
+                            Elem a[M2], o[M2];
 #pragma unroll
-                        for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
-                        step_fiber_dispatch<M, FORM>(I.read, a, (uint32_t)f, o);
+                            for (int q = 0; q < M2; ++q) a[q] = ld_l2(A + f * M2 + q);
+                            step_fiber_dispatch<M, FORM>(I.read, a, (uint32_t)f, o);
 #pragma unroll
-                        for (int x = 0; x < M2; ++x) acc[x].add(o[x]);
+                            for (int x = 0; x < M2; ++x) acc[x].add(o[x]);
+                        }
                     }
                 }
                 const double2 v = block_rows_sum<M2, FORM>(acc, red);
-                if (threadIdx.x < M2) I.partial[(int64_t)t * M2 + threadIdx.x] = v;
+                if (threadIdx.x < M2) {
+                    // half layout: row 2 is the conjugate of row 1 (thread 2 holds an empty sum)
+                    if (!(herm && threadIdx.x == 2)) I.partial[(int64_t)t * M2 + threadIdx.x] = v;
+                    if (herm && threadIdx.x == 1) I.partial[(int64_t)t * M2 + 2] = make_double2(v.x, -v.y);
+                }
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     __threadfence();
@@ -450,13 +655,22 @@ int64_t ipow64(int64_t b, int e) {
     return r;
 }
 
+// canonical prefixes of n digits in the half layout
+int64_t canon64(int n) { return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1; }
+
 // tiles of instance (L, N) at step n for the given tile size
-unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin) {
+unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin, bool herm) {
     if (n < 1 || n > N) return 0;
     int64_t units;
-    if (n < L && n < N) units = ipow64(M2, n);                  // growth: input entries
-    else if (n < N) units = ipow64(M2, L - 1);                  // step: fibers
-    else units = ipow64(M2, read_nin - 1);                      // readout: fibers
+    if (herm) {
+        if (n < L && n < N) units = 4 * canon64(n - 1);         // growth: stored input entries
+        else if (n < N) units = canon64(L - 1);                 // step: canonical prefixes
+        else units = canon64(read_nin - 1);                     // readout: canonical prefixes
+    } else {
+        if (n < L && n < N) units = ipow64(M2, n);              // growth: input entries
+        else if (n < N) units = ipow64(M2, L - 1);              // step: fibers
+        else units = ipow64(M2, read_nin - 1);                  // readout: fibers
+    }
     return (unsigned)((units + te - 1) / te);
 }
 
@@ -543,7 +757,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
             P.resident.push_back(i);
         } else {
             P.tiled.push_back(i);
-            read_tiles[i] = tiles_at(M2, I.L, I.N, I.N, te, I.read.n_in);
+            read_tiles[i] = tiles_at(M2, I.L, I.N, I.N, te, I.read.n_in, I.herm != 0);
             part_total += read_tiles[i];
         }
     }
@@ -581,7 +795,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
         int64_t acc = 0;
         for (int k = 0; k < nt; ++k) {
             const BatchInst& I = P.inst[P.tiled[k]];
-            const unsigned t = tiles_at(M2, I.L, I.N, n, te, I.read.n_in);
+            const unsigned t = tiles_at(M2, I.L, I.N, n, te, I.read.n_in, I.herm != 0);
             ntl[(size_t)n * nt + k] = t;
             need[(size_t)n * nt + k] = cum[k];
             ioff[(size_t)n * (nt + 1) + k] = acc;
@@ -720,10 +934,18 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
-        if (ctx_half_layout(ctxs[i]))
-            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: contexts in the Hermitian half layout run alone");
         if (form == QUAPI_DF64)
             return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: the double-float form runs one context at a time");
+        if (ctx_half_layout(ctxs[i])) {  // the half layout stores one of each conjugate pair: rho0 = rho0^dagger
+            const double* r0 = rho0s[i];
+            for (int r = 0; r < M; ++r)
+                for (int q = 0; q < M; ++q) {
+                    const double* a = r0 + 2 * (r * M + q);
+                    const double* b = r0 + 2 * (q * M + r);
+                    if (std::fabs(a[0] - b[0]) > 1e-12 || std::fabs(a[1] + b[1]) > 1e-12)
+                        return record_error(nullptr, QUAPI_ERR_ARG, "batch: the Hermitian half layout needs a Hermitian rho0");
+                }
+        }
         uids[i] = ctx_uid(ctxs[i]);
         Ns[i] = nsteps_each[i];
     }

@@ -24,6 +24,7 @@
 #include <cstdio>
 
 #include "quapi_internal.h"
+#include "half_layout.cuh"
 
 namespace quapi {
 
@@ -604,118 +605,6 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
 // (1, conj f), (0, f), (3, f) (and the conjugate entries (0/3, conj f) when
 // those are stored); the readout adds row 1 over f and conj f and twice the
 // real part of the diagonal rows (their conjugate partners are conjugates).
-
-__host__ __device__ __forceinline__ int64_t half_count(int n) {  // C(n)
-    return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1;
-}
-__host__ __device__ __forceinline__ int64_t half_entries(int n) {  // stored entries of n digits
-    return n == 0 ? 1 : 4 * half_count(n - 1);
-}
-
-// canonical position c among n-digit prefixes -> plain digits and whether the
-// prefix is its own conjugate (all digits 0 or 3).  32-bit: n <= 15.
-__device__ __forceinline__ uint32_t half_count32(int n) { return ((1u << (2 * n)) + (1u << n)) >> 1; }
-
-__device__ __forceinline__ void half_decode(uint32_t c, int n, uint32_t& plain, bool& sc) {
-    uint32_t p = 0;
-    for (int level = n; level >= 1; --level) {
-        const uint32_t r1 = 1u << (2 * (level - 1));
-        if (c < r1) {  // digit 1, the rest is plain
-            plain = (p << (2 * level)) | r1 | c;
-            sc = false;
-            return;
-        }
-        c -= r1;
-        const uint32_t cn1 = half_count32(level - 1);
-        if (c < cn1) {
-            p = p << 2;
-        } else {
-            c -= cn1;
-            p = (p << 2) | 3u;
-        }
-    }
-    plain = p;
-    sc = true;
-}
-
-// half_decode together with the prefix fh = f >> 2 (f without its last digit,
-// n - 1 digits): its canonical position h and whether it is its own conjugate.
-// The digits above f's first digit 1 are shared with fh, so one walk down the
-// levels gives both positions (fh of a canonical f is canonical).
-__device__ __forceinline__ void half_decode_pair(uint32_t c, int n, uint32_t& plain, bool& sc, uint32_t& h,
-                                                 bool& shc) {
-    uint32_t p = 0, hoff = 0;
-    for (int level = n; level >= 1; --level) {
-        const uint32_t r1 = 1u << (2 * (level - 1));
-        if (c < r1) {  // digit 1 at this level, the rest is plain
-            plain = (p << (2 * level)) | r1 | c;
-            sc = false;
-            h = hoff + (c >> 2);      // level >= 2: fh keeps the digit 1 and the plain rest c >> 2
-            shc = (level == 1);       // level 1: the digit 1 was f's last digit, fh is all 0s and 3s
-            return;
-        }
-        c -= r1;
-        const uint32_t cn1 = half_count32(level - 1);
-        // fh's layout at level - 1: [digit 1: r1 / 4][digit 0: C(level - 2)][digit 3: C(level - 2)]
-        const uint32_t skip = (level >= 2) ? (r1 >> 2) : 0u;
-        if (c < cn1) {
-            p = p << 2;
-            hoff += skip;
-        } else {
-            c -= cn1;
-            p = (p << 2) | 3u;
-            hoff += (level >= 2) ? skip + half_count32(level - 2) : 0u;
-        }
-    }
-    plain = p;
-    sc = true;
-    h = hoff;
-    shc = true;
-}
-
-// canonical position of a canonical n-digit prefix given by its plain digits
-__device__ __forceinline__ uint32_t half_position(uint32_t h, int n) {
-    uint32_t idx = 0;
-    for (int level = n; level >= 1; --level) {
-        const uint32_t d = (h >> (2 * (level - 1))) & 3u;
-        const uint32_t r1 = 1u << (2 * (level - 1));
-        if (d == 1u) return idx + (h & (r1 - 1u));
-        idx += r1;
-        if (d == 3u) idx += half_count32(level - 1);
-    }
-    return idx;
-}
-
-__device__ __forceinline__ bool self_conjugate(uint32_t h, int n) {  // every digit 0 or 3
-    const uint32_t mask = (n >= 16) ? 0x55555555u : ((1u << (2 * n)) - 1u) & 0x55555555u;
-    return ((h ^ (h >> 1)) & mask) == 0u;
-}
-
-__device__ __forceinline__ uint32_t conj_digits(uint32_t f) {
-    return ((f & 0x55555555u) << 1) | ((f & 0xAAAAAAAAu) >> 1);
-}
-
-__device__ __forceinline__ double2 conjv(double2 v) { return make_double2(v.x, -v.y); }
-__device__ __forceinline__ float2 conjv(float2 v) { return make_float2(v.x, -v.y); }
-__device__ __forceinline__ df2 conjv(df2 v) {
-    v.h.y = -v.h.y;
-    v.l.y = -v.l.y;
-    return v;
-}
-__device__ __forceinline__ double2 twice_real(double2 v) { return make_double2(2.0 * v.x, 0.0); }
-__device__ __forceinline__ float2 twice_real(float2 v) { return make_float2(2.f * v.x, 0.f); }
-__device__ __forceinline__ df2 twice_real(df2 v) {
-    v.h = make_float2(2.f * v.h.x, 0.f);
-    v.l = make_float2(2.f * v.l.x, 0.f);
-    return v;
-}
-__device__ __forceinline__ double2 real_part(double2 v) { return make_double2(v.x, 0.0); }
-__device__ __forceinline__ float2 real_part(float2 v) { return make_float2(v.x, 0.f); }
-__device__ __forceinline__ df2 real_part(df2 v) {
-    v.h.y = 0.f;
-    v.l.y = 0.f;
-    return v;
-}
 
 // the 4 entries of fiber c (aligned: FP32 as two 16-byte loads)
 template <int FORM>

@@ -675,6 +675,7 @@ quapi_status batch_describe(const quapi_ctx* c, int64_t N, BatchInst* inst, int*
     inst->buf[1] = c->buf[1];
     inst->L = c->L;
     inst->N = (int)N;
+    inst->herm = c->herm ? 1 : 0;
     inst->self0_idx = eta_self0(c->L);
     inst->eta = c->d_eta;
     inst->s = c->d_s;

@@ -275,6 +275,7 @@ struct OpRef {
 struct BatchInst {
     void* buf[2];
     int L, N, resident;
+    int herm;                // tensors in the Hermitian half layout (M = 2)
     int self0_idx;
     const double2* eta;
     const double* s;

@@ -30,35 +30,38 @@ def _c(v):
     return np.array([complex(a, b) for a, b in v])
 
 
-def _ctxs(q, probs, prec, tune=0):
+def _ctxs(q, probs, prec, tune=0, hermitian=0):
     return [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
-                          q.quapi_opts_init(precision=prec, tune=tune)) for p in probs]
+                          q.quapi_opts_init(precision=prec, tune=tune, hermitian=hermitian)) for p in probs]
 
 
+@pytest.mark.parametrize("half", [0, 1])
 @pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
-def test_batched_256_against_stored_oracle(q, prec, tol):
+def test_batched_256_against_stored_oracle(q, prec, tol, half):
+    """half = 1: the tiled instances keep their tensors in the Hermitian half layout."""
     probs = wl.batched_256()
     with open(os.path.join(HERE, "golden", "batched_256.json")) as fh:
         g = json.load(fh)
-    ctxs = _ctxs(q, probs, prec)
+    ctxs = _ctxs(q, probs, prec, hermitian=half)
     try:
         for rep in range(2):  # second call replays the captured graph
             got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], [p.N for p in probs])
             worst = max(float(np.abs(r - _c(x["rho"]).reshape(2, 2)).max()) for r, x in zip(got, g["instances"]))
-            print(f"batched_256 precision {prec} call {rep}: max abs error vs oracle = {worst:.3e}")
+            print(f"batched_256 precision {prec} half layout {half} call {rep}: max abs error vs oracle = {worst:.3e}")
             assert worst <= tol
     finally:
         for c in ctxs:
             q.quapi_destroy(c)
 
 
+@pytest.mark.parametrize("half", [0, 1])
 @pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
-def test_batched_mixed_final_steps(q, prec, tol):
-    """Final steps 0, 1, below and above L, several memory lengths, M = 2."""
+def test_batched_mixed_final_steps(q, prec, tol, half):
+    """Final steps 0, 1, below and above L, several memory lengths, M = 2 (readouts in the growth phase too)."""
     base = wl.batched_256(n=12, seed=3)
     Ns = [0, 1, 2, 3, 5, 9, 11, 12, 20, 33, 47, 60]
     probs = base
-    ctxs = _ctxs(q, probs, prec)
+    ctxs = _ctxs(q, probs, prec, hermitian=half)
     try:
         got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], Ns)
     finally:
@@ -67,6 +70,26 @@ def test_batched_mixed_final_steps(q, prec, tol):
     for p, N, r in zip(probs, Ns, got):
         want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, [N])[N]
         assert np.abs(r - want).max() <= tol, (p.L, N)
+
+
+def test_batched_half_and_full_layouts_together(q):
+    """Half-layout and full-layout contexts in one batch, tiled memory lengths 6..12, and L = 1 (a
+    one-digit tensor whose prefixes have no digits): each instance matches the oracle."""
+    probs = wl.batched_256(n=10, seed=17, N=30)
+    Ls = [1, 6, 7, 8, 9, 10, 11, 12, 7, 9]
+    for p, L in zip(probs, Ls):
+        p.L = L
+    ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                          q.quapi_opts_init(precision=64, hermitian=i % 2)) for i, p in enumerate(probs)]
+    Ns = [30, 30, 25, 30, 12, 30, 11, 30, 7, 30]
+    try:
+        got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], Ns)
+    finally:
+        for c in ctxs:
+            q.quapi_destroy(c)
+    for p, N, r in zip(probs, Ns, got):
+        want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, [N])[N]
+        assert np.abs(r - want).max() <= 1e-12, (p.L, N)
 
 
 def test_batched_three_level(q):
@@ -88,9 +111,10 @@ def test_batched_three_level(q):
         assert np.abs(r - want).max() <= 1e-12
 
 
-def test_batched_autotuned_matches(q):
+@pytest.mark.parametrize("half", [0, 1])
+def test_batched_autotuned_matches(q, half):
     probs = wl.batched_256(n=24, seed=9, N=40)
-    ctxs = _ctxs(q, probs, 32, tune=1)
+    ctxs = _ctxs(q, probs, 32, tune=1, hermitian=half)
     try:
         got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], [p.N for p in probs])
     finally:

@@ -116,9 +116,11 @@ def test_half_layout_checkpoint_and_rejections(q):
         a = q.quapi_propagate_resume(c1, [40], 2)
         b = q.quapi_propagate_resume(c2, [40], 2)
         assert np.array_equal(a, b)
+        bad = np.array(p.rho0, dtype=np.complex128).reshape(2, 2).copy()
+        bad[0, 1] += 0.1j  # no longer Hermitian: the half layout cannot hold its tensor
         with pytest.raises(q.QuapiError) as e:
-            q.quapi_propagate_batch([c1], [p.rho0], [10])
-        assert e.value.status == q.QUAPI_ERR_UNSUPPORTED
+            q.quapi_propagate_batch([c1], [bad], [10])
+        assert e.value.status == q.QUAPI_ERR_ARG
     finally:
         q.quapi_destroy(c1)
         q.quapi_destroy(c2)
