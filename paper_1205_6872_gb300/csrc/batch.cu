@@ -13,6 +13,9 @@
 // instance's final step writes one partial sum per tile; the CTA finishing the
 // last tile adds them in tile order (deterministic result).
 //
+// Dynamic shared memory is sized to the largest resident instance (none: 0), and a batch whose tiled
+// instances all use the Hermitian half layout runs a kernel without the full-layout tile code.
+//
 // Launch shape (FPT, group) is chosen per batch signature by timing candidates
 // when tuning is requested (quapi_opts.tune or QUAPI_TUNE=1); the choice is
 // cached in memory and, if QUAPI_TUNE_CACHE names a file, on disk.
@@ -394,8 +397,11 @@ __device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*
     __syncthreads();
 }
 
-template <int M, int FORM, int FPT>
-__global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(BatchArgs args) {
+// HO: every tiled instance of the batch is in the Hermitian half layout (M = 2); the full-layout tile
+// code is left out, which lowers the register need: 4 resident CTAs per SM (256 instances, FP32:
+// 82 ms per batch against 87 ms at 3 CTAs and 91 ms at 5), the general kernel 3.
+template <int M, int FORM, int FPT, bool HO>
+__global__ void __launch_bounds__(kBThreads, HO ? 4 : ((M == 2) ? 3 : 1)) batch_kernel(BatchArgs args) {
     constexpr int M2 = M * M;
     using Elem = typename Form<FORM>::Elem;
     constexpr int TE = kBThreads * FPT;  // fibers (or growth entries) per tile
@@ -468,13 +474,13 @@ __global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(Batc
         void* outv = I.buf[n & 1];
         for (unsigned t = t0; t < t1; ++t) {
             const int64_t base = (int64_t)t * TE + (int64_t)threadIdx.x * FPT;
-            const bool herm = (M == 2) && I.herm;
+            const bool herm = HO || ((M == 2) && I.herm);
             if (herm && n < I.N) {
                 if constexpr (M == 2) {
                     if (n < I.L) herm_grow_tile<FORM, FPT>(I.grow[n], in, outv, n, (int64_t)t * TE);
                     else herm_step_tile<FORM, FPT>(n == I.L ? I.step_first : I.step, in, outv, I.L - 1, (int64_t)t * TE);
                 }
-            } else if (n < I.L && n < I.N) {
+            } else if (!HO && n < I.L && n < I.N) {
                 int64_t S = 1;
                 for (int i = 0; i < n; ++i) S *= M2;
                 const OpTabs<M, FORM> T = tabs_of<M, FORM>(I.grow[n]);
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(Batc
                         for (int x = 0; x < M2; ++x) out[x * S + i] = o[x];
                     }
                 }
-            } else if (n < I.N) {
+            } else if (!HO && n < I.N) {
                 int64_t F = 1;
                 for (int i = 1; i < I.L; ++i) F *= M2;
                 const OpRef& op = (n == I.L) ? I.step_first : I.step;
@@ -549,7 +555,7 @@ __global__ void __launch_bounds__(kBThreads, (M == 2) ? 3 : 1) batch_kernel(Batc
                 for (int x = 0; x < M2; ++x) acc[x].init();
                 if (herm) {
                     if constexpr (M == 2) herm_read_tile<FORM, FPT>(I.read, in, I.read.n_in - 1, (int64_t)t * TE, acc);
-                } else {
+                } else if constexpr (!HO) {
 #pragma unroll
                     for (int u = 0; u < FPT; ++u) {
                         const int64_t f = base + u;
@@ -615,6 +621,7 @@ struct DevBuf {
 
 struct Plan {
     int M = 0, form = 0, fpt = 0, group = 0, n = 0;
+    bool half_only = false;  // every tiled instance in the half layout
     std::vector<uint64_t> uids;
     std::vector<int64_t> Ns;
     std::vector<BatchInst> inst;
@@ -675,7 +682,7 @@ unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin, bool he
 }
 
 template <int M, int FORM, int FPT> cudaError_t launch_batch(Plan& P, cudaStream_t st, bool prepare_only) {
-    auto kern = batch_kernel<M, FORM, FPT>;
+    auto kern = P.half_only ? batch_kernel<M, FORM, FPT, (M == 2)> : batch_kernel<M, FORM, FPT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
     if (e != cudaSuccess) return e;
     if (P.grid == 0) {
@@ -741,7 +748,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     P.group = group;
     P.n = (int)insts.size();
     P.inst = insts;
-    P.smem = kResidentBytes;
+    P.smem = 0;  // the largest resident instance's two tensors (none: no dynamic shared memory)
     const int te = kBThreads * fpt;
     // per-instance buffers
     if ((e = cudaMalloc(&P.d_rho0.p, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
@@ -755,12 +762,15 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
         const bool res = 2 * (size_t)ipow64(M2, I.L) * elt <= (size_t)kResidentBytes;
         if (res) {
             P.resident.push_back(i);
+            P.smem = std::max(P.smem, 2 * (size_t)ipow64(M2, I.L) * elt);
         } else {
             P.tiled.push_back(i);
             read_tiles[i] = tiles_at(M2, I.L, I.N, I.N, te, I.read.n_in, I.herm != 0);
             part_total += read_tiles[i];
         }
     }
+    P.half_only = M == 2 && !P.tiled.empty();
+    for (int i : P.tiled) P.half_only = P.half_only && P.inst[i].herm != 0;
     // counters (done + read_done per instance) and readout partials
     P.cnt_bytes = sizeof(unsigned) * 2 * std::max(P.n, 1);
     if ((e = cudaMalloc(&P.d_cnt.p, P.cnt_bytes)) != cudaSuccess) return e;
