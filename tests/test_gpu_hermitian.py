@@ -87,6 +87,43 @@ def test_half_layout_propagation_small(q, prec):
 
 
 @pytest.mark.parametrize("prec", [64, 32, 48])
+@pytest.mark.parametrize("endpoint", [0, 1])
+def test_half_layout_every_step_both_endpoints(q, endpoint, prec):
+    """Readout at every step (the paper's allPoints), growth included, in both end-point modes."""
+    p = wl.spin_boson_L6()
+    steps = list(range(p.N + 1))
+    want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, steps,
+                            endpoint="strang" if endpoint == 0 else "interior")
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                        q.quapi_opts_init(precision=prec, hermitian=1, endpoint_mode=endpoint))
+    try:
+        got = q.quapi_propagate(ctx, p.rho0, steps, 2)
+    finally:
+        q.quapi_destroy(ctx)
+    err = max(float(np.abs(got[i] - want[k]).max()) for i, k in enumerate(steps))
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [64, 32, 48])
+def test_half_layout_biased_workload_against_stored_oracle(q, prec):
+    """Biased spin-boson (memory length 12, 400 steps, bias 0.5) in the half layout."""
+    p = wl.biased_L12()
+    with open(os.path.join(HERE, "golden", "biased_L12.json")) as fh:
+        g = json.load(fh)
+    steps = [int(k) for k in g["steps"]]
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                        q.quapi_opts_init(precision=prec, hermitian=1))
+    try:
+        got = q.quapi_propagate(ctx, p.rho0, steps, 2)
+    finally:
+        q.quapi_destroy(ctx)
+    worst = max(float(np.abs(got[i] - np.array([complex(a, b) for a, b in g["rho"][str(k)]]).reshape(2, 2)).max())
+                for i, k in enumerate(steps))
+    print(f"biased_L12 half layout precision {prec}: max abs error vs oracle = {worst:.3e}")
+    assert worst <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [64, 32, 48])
 def test_half_layout_bench_workload_against_stored_oracle(q, prec):
     p = wl.spin_boson_L14()
     with open(os.path.join(HERE, "golden", "spin_boson_L14.json")) as fh:
