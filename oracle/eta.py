@@ -44,15 +44,24 @@ from scipy import integrate
 
 OHMIC_EXP = "ohmic_exp"            # J = (pi/2) a w exp(-w/wc)
 SUPEROHMIC_GAUSS = "superohmic_gauss"  # J = a w^3 exp(-(w/wc)^2)  (Eq. superOhmicJwithGaussianCutoff)
+TABULATED = "tabulated"            # J piecewise linear through (0, 0) and the table, 0 above its last node
 
 
 @dataclass(frozen=True)
 class Spectral:
-    """Spectral distribution function J(w) (Eq. spectralDistribution), parametric form."""
+    """Spectral distribution function J(w) (Eq. spectralDistribution): a parametric form, or a
+    table (omega ascending, omega[0] > 0) read as the piecewise-linear function through (0, 0)
+    and (omega[i], values[i]), zero above omega[-1]."""
 
     kind: str
-    a: float
-    wc: float
+    a: float = 0.0
+    wc: float = 1.0
+    omega: tuple = ()
+    values: tuple = ()
+
+    @staticmethod
+    def tabulated(omega, values) -> "Spectral":
+        return Spectral(TABULATED, omega=tuple(float(x) for x in omega), values=tuple(float(x) for x in values))
 
     def J_over_w2(self, w):
         """J(w)/w^2, written so that it stays finite and accurate as w -> 0."""
@@ -61,14 +70,22 @@ class Spectral:
             return (math.pi / 2.0) * self.a * np.exp(-w / self.wc) / w
         if self.kind == SUPEROHMIC_GAUSS:
             return self.a * w * np.exp(-(w / self.wc) ** 2)
+        if self.kind == TABULATED:
+            return self.J(w) / (w * w)
         raise ValueError(f"unknown spectral density kind {self.kind!r}")
 
     def J(self, w):
         w = np.asarray(w, dtype=np.float64)
+        if self.kind == TABULATED:
+            xp = np.concatenate([[0.0], np.asarray(self.omega)])
+            fp = np.concatenate([[0.0], np.asarray(self.values)])
+            return np.interp(w, xp, fp, right=0.0)
         return self.J_over_w2(w) * w * w
 
     def omega_max(self) -> float:
-        """Upper frequency limit beyond which J's cutoff factor is below ~1e-18."""
+        """Upper frequency limit: the table's last node, or where J's cutoff factor is below ~1e-18."""
+        if self.kind == TABULATED:
+            return float(self.omega[-1])
         if self.kind == OHMIC_EXP:
             return 42.0 * self.wc
         return 7.0 * self.wc
@@ -107,6 +124,8 @@ def _quad(f, a, b, breaks):
 
 
 def _breaks(spec: Spectral, wmax: float):
+    if spec.kind == TABULATED:  # J has a kink at every node
+        return [x for x in spec.omega if 0.0 < x < wmax]
     # a few fixed interior break points around the cutoff scale help QUADPACK
     pts = [x * spec.wc for x in (0.25, 1.0, 3.0, 8.0, 20.0) if x * spec.wc < wmax]
     return pts
