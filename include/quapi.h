@@ -50,16 +50,26 @@ typedef enum {
     QUAPI_ERR_UNSUPPORTED = 5   /* valid request this build does not implement */
 } quapi_status;
 
-/* Parametric spectral densities J(w) (Eq. spectralDistribution). */
+/* Spectral densities J(w) (Eq. spectralDistribution): two parametric forms, or a table. */
 typedef enum {
     QUAPI_J_OHMIC_EXP = 0,        /* J = (pi/2) a w exp(-w/wc)                               */
-    QUAPI_J_SUPEROHMIC_GAUSS = 1  /* J = a w^3 exp(-(w/wc)^2)  (Eq. superOhmicJwithGaussianCutoff) */
+    QUAPI_J_SUPEROHMIC_GAUSS = 1, /* J = a w^3 exp(-(w/wc)^2)  (Eq. superOhmicJwithGaussianCutoff) */
+    QUAPI_J_TABULATED = 2         /* J given at n frequencies: piecewise linear through (0, 0) and
+                                     (omega[i], values[i]), zero above omega[n-1]               */
 } quapi_jkind;
 
 typedef struct {
     int kind;    /* quapi_jkind */
-    double a;    /* prefactor (alpha for Ohmic, xi / A for super-Ohmic), >= 0 */
-    double wc;   /* cutoff frequency, > 0 */
+    double a;    /* parametric kinds: prefactor (alpha for Ohmic, xi / A for super-Ohmic), >= 0 */
+    double wc;   /* parametric kinds: cutoff frequency, > 0 */
+    /* QUAPI_J_TABULATED only (ignored otherwise).  Host arrays owned by the caller and read
+       during quapi_setup only.  omega: n strictly ascending finite frequencies, omega[0] > 0;
+       values: J at those frequencies, finite and >= 0; 1 <= n <= 65536.  The eta integrals run
+       over [0, omega[n-1]] with quadrature panels aligned to the table's nodes.  Any violation
+       is QUAPI_ERR_ARG. */
+    const double* omega;
+    const double* values;
+    int n;
 } quapi_spectral;
 
 enum {

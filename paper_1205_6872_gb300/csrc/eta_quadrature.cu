@@ -11,6 +11,8 @@
 //     (1/pi) int J/w^2 [coth(beta w/2) (1 - cos w w) + i (sin w w - w w)] dw
 // Each is evaluated with a composite Gauss-Legendre rule (16 nodes per panel)
 // on [0, w_max]; one CTA per eta, FP64 accumulation, fixed-order reduction.
+// A tabulated J (piecewise linear) gets panels that never straddle a table
+// node, so the rule sees a smooth integrand on every panel.
 #include <cmath>
 #include <vector>
 
@@ -43,50 +45,32 @@ __device__ __forceinline__ double sin_minus_x(double x) {
     return acc;
 }
 
-__global__ void __launch_bounds__(kEtaThreads) eta_kernel(const EtaJob* __restrict__ jobs, int kind,
-                                                          double a, double wc, double beta,
-                                                          double wmax, int panels,
-                                                          const double* __restrict__ gl, int gl_n,
-                                                          double2* __restrict__ out) {
-    __shared__ double sx[kMaxGL], sw[kMaxGL];
+// One quadrature node: adds (1/pi) wt J(w)/w^2 times the box kernel of job jb at frequency w.
+__device__ __forceinline__ void eta_node(const EtaJob& jb, double beta, double w, double jw, double& acc_re,
+                                         double& acc_im) {
+    const double cth = 1.0 / tanh(0.5 * beta * w);
+    if (jb.w2 < 0.0) {  // self box
+        const double sh = sin(0.5 * w * jb.w1);
+        acc_re += jw * cth * 2.0 * sh * sh;
+        acc_im += jw * sin_minus_x(w * jb.w1);
+    } else {
+        const double c = jw * 4.0 * sin(0.5 * w * jb.w1) * sin(0.5 * w * jb.w2);
+        double sd, cd;
+        sincos(w * jb.D, &sd, &cd);
+        acc_re += c * cth * cd;
+        acc_im -= c * sd;
+    }
+}
+
+// Fixed-order block reduction of the two accumulators into out.
+__device__ __forceinline__ void eta_reduce(double acc_re, double acc_im, double2* out) {
     __shared__ double red_re[kEtaThreads / 32], red_im[kEtaThreads / 32];
-    if (threadIdx.x < gl_n) {
-        sx[threadIdx.x] = gl[threadIdx.x];
-        sw[threadIdx.x] = gl[gl_n + threadIdx.x];
-    }
-    __syncthreads();
-    const EtaJob jb = jobs[blockIdx.x];
-    const bool self_box = jb.w2 < 0.0;
-    const double h = wmax / panels;
-    const double inv_pi = 0.31830988618379067;
-    double acc_re = 0.0, acc_im = 0.0;
-    const int64_t nodes = (int64_t)panels * gl_n;
-    for (int64_t q = threadIdx.x; q < nodes; q += kEtaThreads) {
-        int panel = (int)(q / gl_n);
-        int i = (int)(q - (int64_t)panel * gl_n);
-        double w = h * (panel + 0.5 * (1.0 + sx[i]));
-        double wt = 0.5 * h * sw[i];
-        double jw = j_over_w2(kind, a, wc, w) * inv_pi * wt;
-        double cth = 1.0 / tanh(0.5 * beta * w);
-        if (self_box) {
-            double sh = sin(0.5 * w * jb.w1);
-            acc_re += jw * cth * 2.0 * sh * sh;
-            acc_im += jw * sin_minus_x(w * jb.w1);
-        } else {
-            double c = jw * 4.0 * sin(0.5 * w * jb.w1) * sin(0.5 * w * jb.w2);
-            double sd, cd;
-            sincos(w * jb.D, &sd, &cd);
-            acc_re += c * cth * cd;
-            acc_im -= c * sd;
-        }
-    }
-    // fixed-order reduction: warp tree, then warp 0 over the warp sums
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         acc_re += __shfl_down_sync(0xffffffffu, acc_re, off);
         acc_im += __shfl_down_sync(0xffffffffu, acc_im, off);
     }
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
         red_re[warp] = acc_re;
         red_im[warp] = acc_im;
@@ -98,8 +82,62 @@ __global__ void __launch_bounds__(kEtaThreads) eta_kernel(const EtaJob* __restri
             r += red_re[k];
             m += red_im[k];
         }
-        out[blockIdx.x] = make_double2(r, m);
+        *out = make_double2(r, m);
     }
+}
+
+// Tabulated J: panels [pw[p], pw[p+1]] each inside one segment of the table, J linear on the
+// panel between its end values pj[p], pj[p+1].
+__global__ void __launch_bounds__(kEtaThreads) eta_kernel_tab(const EtaJob* __restrict__ jobs, double beta,
+                                                              const double* __restrict__ pw,
+                                                              const double* __restrict__ pj, int panels,
+                                                              const double* __restrict__ gl, int gl_n,
+                                                              double2* __restrict__ out) {
+    __shared__ double sx[kMaxGL], sw[kMaxGL];
+    if (threadIdx.x < gl_n) {
+        sx[threadIdx.x] = gl[threadIdx.x];
+        sw[threadIdx.x] = gl[gl_n + threadIdx.x];
+    }
+    __syncthreads();
+    const EtaJob jb = jobs[blockIdx.x];
+    const double inv_pi = 0.31830988618379067;
+    double acc_re = 0.0, acc_im = 0.0;
+    const int64_t nodes = (int64_t)panels * gl_n;
+    for (int64_t q = threadIdx.x; q < nodes; q += kEtaThreads) {
+        const int panel = (int)(q / gl_n);
+        const int i = (int)(q - (int64_t)panel * gl_n);
+        const double lo = pw[panel], h = pw[panel + 1] - lo;
+        const double t = 0.5 * (1.0 + sx[i]);
+        const double w = lo + h * t;
+        const double J = pj[panel] + (pj[panel + 1] - pj[panel]) * t;
+        eta_node(jb, beta, w, J / (w * w) * inv_pi * (0.5 * h * sw[i]), acc_re, acc_im);
+    }
+    eta_reduce(acc_re, acc_im, out + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kEtaThreads) eta_kernel(const EtaJob* __restrict__ jobs, int kind,
+                                                          double a, double wc, double beta,
+                                                          double wmax, int panels,
+                                                          const double* __restrict__ gl, int gl_n,
+                                                          double2* __restrict__ out) {
+    __shared__ double sx[kMaxGL], sw[kMaxGL];
+    if (threadIdx.x < gl_n) {
+        sx[threadIdx.x] = gl[threadIdx.x];
+        sw[threadIdx.x] = gl[gl_n + threadIdx.x];
+    }
+    __syncthreads();
+    const EtaJob jb = jobs[blockIdx.x];
+    const double h = wmax / panels;
+    const double inv_pi = 0.31830988618379067;
+    double acc_re = 0.0, acc_im = 0.0;
+    const int64_t nodes = (int64_t)panels * gl_n;
+    for (int64_t q = threadIdx.x; q < nodes; q += kEtaThreads) {
+        const int panel = (int)(q / gl_n);
+        const int i = (int)(q - (int64_t)panel * gl_n);
+        const double w = h * (panel + 0.5 * (1.0 + sx[i]));
+        eta_node(jb, beta, w, j_over_w2(kind, a, wc, w) * inv_pi * (0.5 * h * sw[i]), acc_re, acc_im);
+    }
+    eta_reduce(acc_re, acc_im, out + blockIdx.x);
 }
 
 }  // namespace
@@ -139,6 +177,16 @@ cudaError_t launch_eta_quadrature(const EtaJob* jobs_dev, int njobs, int kind, d
     double wmax = (kind == QUAPI_J_OHMIC_EXP) ? 46.0 * wc : 7.5 * wc;
     eta_kernel<<<njobs, kEtaThreads, 0, st>>>(jobs_dev, kind, a, wc, beta, wmax, panels, gl_dev, gl_n,
                                               eta_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eta_quadrature_tab(const EtaJob* jobs_dev, int njobs, double beta, const double* pw_dev,
+                                      const double* pj_dev, int panels, const double* gl_dev, int gl_n,
+                                      double2* eta_out, cudaStream_t st) {
+    if (njobs <= 0) return cudaSuccess;
+    if (gl_n > kMaxGL || panels < 1) return cudaErrorInvalidValue;
+    eta_kernel_tab<<<njobs, kEtaThreads, 0, st>>>(jobs_dev, beta, pw_dev, pj_dev, panels, gl_dev, gl_n, eta_out);
     count_launch();
     return cudaGetLastError();
 }

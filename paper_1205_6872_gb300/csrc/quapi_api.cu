@@ -53,6 +53,9 @@ int64_t ipow(int64_t b, int e) {
 }
 
 int max_dkmax(int M) { return M == 2 ? 16 : 10; }
+constexpr int kMaxTableNodes = 65536;          // tabulated J: largest table
+constexpr int64_t kMaxEtaPanels = int64_t(1) << 22;  // tabulated J: largest panel count
+
 // stored entries of an n-digit tensor in the Hermitian half layout: 4 C(n-1), C(m) = (4^m + 2^m)/2
 int64_t half_entries(int n) {
     if (n == 0) return 1;
@@ -253,10 +256,21 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     if (stc != QUAPI_OK) return stc;
     if (!eta_host) {
         if (!J) return fail(nullptr, QUAPI_ERR_ARG, "J must not be NULL");
-        if (J->kind != QUAPI_J_OHMIC_EXP && J->kind != QUAPI_J_SUPEROHMIC_GAUSS)
+        if (J->kind == QUAPI_J_TABULATED) {
+            if (!J->omega || !J->values || J->n < 1 || J->n > kMaxTableNodes)
+                return fail(nullptr, QUAPI_ERR_ARG, "tabulated J needs 1..65536 nodes and non-NULL arrays");
+            for (int i = 0; i < J->n; ++i) {
+                const double w = J->omega[i], v = J->values[i];
+                if (!std::isfinite(w) || !std::isfinite(v) || v < 0.0 || w <= (i ? J->omega[i - 1] : 0.0))
+                    return fail(nullptr, QUAPI_ERR_ARG,
+                                "tabulated J needs finite, strictly ascending omega > 0 and finite values >= 0");
+            }
+        } else if (J->kind == QUAPI_J_OHMIC_EXP || J->kind == QUAPI_J_SUPEROHMIC_GAUSS) {
+            if (!(J->a >= 0.0) || !(J->wc > 0.0) || !std::isfinite(J->a) || !std::isfinite(J->wc))
+                return fail(nullptr, QUAPI_ERR_ARG, "spectral density needs a >= 0 and wc > 0");
+        } else {
             return fail(nullptr, QUAPI_ERR_ARG, "unknown spectral density kind");
-        if (!(J->a >= 0.0) || !(J->wc > 0.0) || !std::isfinite(J->a) || !std::isfinite(J->wc))
-            return fail(nullptr, QUAPI_ERR_ARG, "spectral density needs a >= 0 and wc > 0");
+        }
         if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, QUAPI_ERR_ARG, "beta must be > 0");
     }
     const int M2 = M * M;
@@ -327,6 +341,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
 
     EtaJob* d_jobs = nullptr;
     double* d_gl = nullptr;
+    double* d_pan = nullptr;  // tabulated J: panel end points, then J at them
     if (eta_host) {
         SCHECK(cudaMemcpyAsync(c->d_eta, eta_host, sizeof(double2) * neta, cudaMemcpyHostToDevice, c->st),
                "copy eta");
@@ -345,10 +360,6 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         jobs[eta_self0(L)] = self(0.5 * dt);
         double kmax = 0.0;
         for (const EtaJob& jb : jobs) kmax = std::max(kmax, jb.w2 < 0 ? jb.w1 : jb.D + 0.5 * (jb.w1 + jb.w2));
-        const double wmax = (J->kind == QUAPI_J_OHMIC_EXP) ? 46.0 * J->wc : 7.5 * J->wc;
-        int panels = (int)std::ceil(wmax * kmax / 2.0);
-        panels = std::max(panels, 256);
-        panels = std::min(panels, 1 << 16);
         std::vector<double> gx, gw;
         gauss_legendre_nodes(16, gx, gw);
         std::vector<double> gl(gx);
@@ -357,8 +368,48 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         SCHECK(cudaMalloc(&d_gl, sizeof(double) * gl.size()), "cudaMalloc(GL nodes)");
         SCHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EtaJob) * neta, cudaMemcpyHostToDevice, c->st), "copy jobs");
         SCHECK(cudaMemcpyAsync(d_gl, gl.data(), sizeof(double) * gl.size(), cudaMemcpyHostToDevice, c->st), "copy GL");
-        SCHECK(launch_eta_quadrature(d_jobs, neta, J->kind, J->a, J->wc, beta, panels, d_gl, 16, c->d_eta, c->st),
-               "eta quadrature kernel");
+        if (J->kind == QUAPI_J_TABULATED) {
+            // segments (0, 0) -> (omega[0], values[0]) -> ...; each cut into panels no wider than the
+            // parametric rule's (2 / kmax, at least 256 panels over [0, omega[n-1]])
+            const double wmax = J->omega[J->n - 1];
+            std::vector<double> pw, pj;
+            double t0 = 0.0, j0 = 0.0;
+            for (int k = 0; k < J->n; ++k) {
+                const double t1 = J->omega[k], j1 = J->values[k], len = t1 - t0;
+                const double want = std::max(len * kmax / 2.0, 256.0 * len / wmax);
+                const int64_t m = std::max<int64_t>(1, (int64_t)std::ceil(want));
+                if ((int64_t)pw.size() + m > kMaxEtaPanels) {
+                    cudaFree(d_jobs);
+                    cudaFree(d_gl);
+                    return bail(fail(c, QUAPI_ERR_ARG, "tabulated J too wide for the eta quadrature panels"));
+                }
+                for (int64_t q = 0; q < m; ++q) {
+                    pw.push_back(t0 + len * (double)q / (double)m);
+                    pj.push_back(j0 + (j1 - j0) * (double)q / (double)m);
+                }
+                t0 = t1;
+                j0 = j1;
+            }
+            pw.push_back(t0);
+            pj.push_back(j0);
+            const int panels = (int)pw.size() - 1;
+            pw.insert(pw.end(), pj.begin(), pj.end());
+            SCHECK(cudaMalloc(&d_pan, sizeof(double) * pw.size()), "cudaMalloc(eta panels)");
+            SCHECK(cudaMemcpyAsync(d_pan, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice, c->st),
+                   "copy eta panels");
+            SCHECK(launch_eta_quadrature_tab(d_jobs, neta, beta, d_pan, d_pan + panels + 1, panels, d_gl, 16,
+                                             c->d_eta, c->st),
+                   "eta quadrature kernel (tabulated J)");
+            SCHECK(cudaStreamSynchronize(c->st), "eta quadrature (tabulated J)");  // pw leaves scope
+        } else {
+            const double wmax = (J->kind == QUAPI_J_OHMIC_EXP) ? 46.0 * J->wc : 7.5 * J->wc;
+            int panels = (int)std::ceil(wmax * kmax / 2.0);
+            panels = std::max(panels, 256);
+            panels = std::min(panels, 1 << 16);
+            SCHECK(launch_eta_quadrature(d_jobs, neta, J->kind, J->a, J->wc, beta, panels, d_gl, 16, c->d_eta,
+                                         c->st),
+                   "eta quadrature kernel");
+        }
     }
 
     // factor tables of every operation, one launch
@@ -399,6 +450,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     cudaFree(d_descs);
     if (d_jobs) cudaFree(d_jobs);
     if (d_gl) cudaFree(d_gl);
+    if (d_pan) cudaFree(d_pan);
     if (c->tune) {
         quapi_status ts = tune_step(c);
         if (ts != QUAPI_OK) return bail(ts);

@@ -202,6 +202,10 @@ struct EtaJob {
 cudaError_t launch_eta_quadrature(const EtaJob* jobs_dev, int njobs, int kind, double a, double wc,
                                   double beta, int panels, const double* gl_dev, int gl_n,
                                   double2* eta_out, cudaStream_t st);
+// tabulated J: panel end points pw[0..panels] and J at them pj[0..panels] (J linear on each panel)
+cudaError_t launch_eta_quadrature_tab(const EtaJob* jobs_dev, int njobs, double beta, const double* pw_dev,
+                                      const double* pj_dev, int panels, const double* gl_dev, int gl_n,
+                                      double2* eta_out, cudaStream_t st);
 void gauss_legendre_nodes(int n, std::vector<double>& x, std::vector<double>& w);
 
 cudaError_t launch_propagator(const double2* H_dev, int M, double dt, double2* U_dev, double2* K_dev,

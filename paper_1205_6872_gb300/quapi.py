@@ -29,13 +29,15 @@ STATUS_NAMES = {0: "QUAPI_OK", 1: "QUAPI_ERR_ARG", 2: "QUAPI_ERR_OOM", 3: "QUAPI
 
 QUAPI_J_OHMIC_EXP = 0
 QUAPI_J_SUPEROHMIC_GAUSS = 1
+QUAPI_J_TABULATED = 2
 QUAPI_FP64 = 64
 QUAPI_FP32 = 32
 QUAPI_DF64 = 48
 QUAPI_ENDPOINT_STRANG = 0
 QUAPI_ENDPOINT_INTERIOR = 1
 
-JKIND = {"ohmic_exp": QUAPI_J_OHMIC_EXP, "superohmic_gauss": QUAPI_J_SUPEROHMIC_GAUSS}
+JKIND = {"ohmic_exp": QUAPI_J_OHMIC_EXP, "superohmic_gauss": QUAPI_J_SUPEROHMIC_GAUSS,
+         "tabulated": QUAPI_J_TABULATED}
 
 EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_setup", "quapi_setup_eta",
             "quapi_propagate", "quapi_propagate_device", "quapi_step_device",
@@ -45,7 +47,9 @@ EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_setup", "quapi_setup
 
 
 class quapi_spectral(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("wc", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("a", ctypes.c_double), ("wc", ctypes.c_double),
+                ("omega", ctypes.POINTER(ctypes.c_double)), ("values", ctypes.POINTER(ctypes.c_double)),
+                ("n", ctypes.c_int)]
 
 
 class quapi_opts(ctypes.Structure):
@@ -162,12 +166,19 @@ def quapi_query_memory(M, dkmax, precision=QUAPI_FP64):
     return t.value, tot.value
 
 
-def quapi_setup(s, H, jkind, a, wc, beta, dt, dkmax, opts=None):
-    """Returns an opaque context handle (int); release it with quapi_destroy."""
+def quapi_setup(s, H, jkind, a, wc, beta, dt, dkmax, opts=None, omega=None, values=None):
+    """Returns an opaque context handle (int); release it with quapi_destroy.
+    jkind "tabulated": J given by the arrays omega (ascending, > 0) and values; a and wc unused."""
     s = np.ascontiguousarray(np.asarray(s, dtype=np.float64))
     M = s.size
     Hc = _c128(H, M * M)
     J = quapi_spectral(JKIND.get(jkind, jkind) if isinstance(jkind, str) else int(jkind), float(a), float(wc))
+    if omega is not None:
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        va = np.ascontiguousarray(np.asarray(values, dtype=np.float64))
+        if om.shape != va.shape:
+            raise ValueError("omega and values must have the same length")
+        J.omega, J.values, J.n = _dp(om), _dp(va), int(om.size)
     o = opts if opts is not None else quapi_opts_init()
     ctx = ctypes.c_void_p()
     _check(load().quapi_setup(_dp(s), M, _dp(Hc.view(np.float64)), ctypes.byref(J), float(beta), float(dt),

@@ -71,3 +71,34 @@ def test_opts_defaults(lib_path):
     o = quapi.quapi_opts_init()
     assert o.precision == quapi.QUAPI_FP64 and o.endpoint_mode == quapi.QUAPI_ENDPOINT_STRANG
     assert not o.workspace and o.workspace_bytes == 0
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """sizeof / offsetof of the ABI structs from a C compiler against the ctypes binding."""
+    from paper_1205_6872_gb300 import quapi
+    src = tmp_path / "layout.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "quapi.h"
+int main(void) {
+    printf("spectral %zu %zu %zu %zu %zu %zu %zu\n", sizeof(quapi_spectral), offsetof(quapi_spectral, kind),
+           offsetof(quapi_spectral, a), offsetof(quapi_spectral, wc), offsetof(quapi_spectral, omega),
+           offsetof(quapi_spectral, values), offsetof(quapi_spectral, n));
+    printf("opts %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(quapi_opts), offsetof(quapi_opts, precision),
+           offsetof(quapi_opts, endpoint_mode), offsetof(quapi_opts, cuda_stream), offsetof(quapi_opts, tune),
+           offsetof(quapi_opts, workspace), offsetof(quapi_opts, workspace_bytes), offsetof(quapi_opts, hermitian));
+    return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = dict(l.split(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                        check=True).stdout.strip().splitlines())
+    S = quapi.quapi_spectral
+    want_s = [ctypes.sizeof(S)] + [getattr(S, f).offset for f in ("kind", "a", "wc", "omega", "values", "n")]
+    assert [int(x) for x in lines["spectral"].split()] == want_s
+    O = quapi.quapi_opts
+    want_o = [ctypes.sizeof(O)] + [getattr(O, f).offset for f in ("precision", "endpoint_mode", "cuda_stream", "tune",
+                                                                    "workspace", "workspace_bytes", "hermitian")]
+    assert [int(x) for x in lines["opts"].split()] == want_o

@@ -71,6 +71,83 @@ def test_eta_workloads(q, name):
     assert np.abs(got - want).max() <= 1e-14 + 1e-13 * np.abs(want).max()
 
 
+def _tab_ctx(q, spec, beta, L, prec=64, dt=0.1):
+    pr = _problem(2)
+    return q.quapi_setup(pr["s"], pr["H"], "tabulated", 0.0, 1.0, beta, dt, L,
+                         q.quapi_opts_init(precision=prec), omega=spec.omega, values=spec.values)
+
+
+@pytest.mark.parametrize("table", ["ramp", "ohmic"])
+@pytest.mark.parametrize("beta", [0.7, 5.0])
+def test_eta_tabulated_matches_oracle(q, table, beta):
+    """Tabulated J: the device quadrature (panels aligned to the table) against the oracle's."""
+    L = 6
+    if table == "ramp":
+        om = np.linspace(3.0, 21.0, 7)
+        spec = Spectral.tabulated(om, 0.4 * om)
+    else:
+        om = np.linspace(0.5, 100.0, 200)
+        spec = Spectral.tabulated(om, Spectral("ohmic_exp", 0.3, 5.0).J(om))
+    ctx = _tab_ctx(q, spec, beta, L)
+    try:
+        got = q.quapi_get_eta(ctx, L)
+    finally:
+        q.quapi_destroy(ctx)
+    want = oracle.pack_eta(oracle.eta_table(spec, beta, 0.1, L))
+    assert np.abs(got - want).max() <= 1e-14 + 1e-13 * np.abs(want).max()
+
+
+def test_eta_tabulated_ramp_zero_temperature_closed_form(q):
+    """J = c w on [0, Om] at beta = 1e7 (thermal part ~ 1/beta^2): the device eta against the sine and
+    cosine integral forms of the self box and of the interior neighbour pair."""
+    from test_oracle_eta import _ramp_pair, _ramp_self
+    c, Om, dt, L = 0.4, 21.0, 0.1, 3
+    om = np.linspace(Om / 5, Om, 5)
+    ctx = _tab_ctx(q, Spectral.tabulated(om, c * om), 1e7, L, dt=dt)
+    try:
+        got = q.quapi_get_eta(ctx, L)
+    finally:
+        q.quapi_destroy(ctx)
+    # packed layout: interior[0..L], point0[0..L-1], end_self, end[0..L-1], end_point0[0..L-1], self0
+    assert abs(got[0] - _ramp_self(c, Om, dt)) <= 1e-13
+    assert abs(got[1] - _ramp_pair(c, Om, dt, dt, dt)) <= 1e-13
+    assert abs(got[2 * L + 1] - _ramp_self(c, Om, 0.5 * dt)) <= 1e-13
+    assert abs(got[-1] - _ramp_self(c, Om, 0.5 * dt)) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
+def test_tabulated_propagation_matches_oracle(q, prec, tol):
+    pr = _problem(2)
+    om = np.linspace(0.25, 60.0, 240)
+    spec = Spectral.tabulated(om, Spectral("ohmic_exp", 0.3, 5.0).J(om))
+    L, steps = 5, [0, 1, 4, 5, 6, 20, 40]
+    want = oracle.propagate(pr["s"], pr["H"], spec, pr["beta"], pr["dt"], L, pr["rho0"], steps)
+    ctx = _tab_ctx(q, spec, pr["beta"], L, prec=prec, dt=pr["dt"])
+    try:
+        got = q.quapi_propagate(ctx, pr["rho0"], steps, 2)
+    finally:
+        q.quapi_destroy(ctx)
+    for i, k in enumerate(steps):
+        assert np.abs(got[i] - want[k]).max() <= tol, k
+
+
+def test_tabulated_argument_errors(q):
+    pr = _problem(2)
+    bad = [([1.0, 0.5], [1.0, 1.0]),    # not ascending
+           ([0.0, 1.0], [0.0, 1.0]),    # omega[0] not > 0
+           ([1.0, 2.0], [1.0, -1.0]),   # negative J
+           ([1.0, np.inf], [1.0, 1.0]),
+           ([], [])]
+    for om, va in bad:
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_setup(pr["s"], pr["H"], "tabulated", 0.0, 1.0, 1.0, 0.1, 3, q.quapi_opts_init(),
+                          omega=om, values=va)
+        assert e.value.status == q.QUAPI_ERR_ARG, (om, va)
+    with pytest.raises(q.QuapiError) as e:  # tabulated kind without a table
+        q.quapi_setup(pr["s"], pr["H"], "tabulated", 0.0, 1.0, 1.0, 0.1, 3, q.quapi_opts_init())
+    assert e.value.status == q.QUAPI_ERR_ARG
+
+
 @pytest.mark.parametrize("M", [2, 3])
 def test_propagator_matches_oracle(q, M):
     pr = _problem(M)
