@@ -57,12 +57,22 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("propagate.cu", "half_layout.cuh", "quapi_internal.h")
+
+
+def kernel_source_sha():
+    """sha256[:16] over the step kernels' source files (propagate.cu, half_layout.cuh, quapi_internal.h)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1205_6872_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(kernel_key):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source is unchanged."""
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
-    src = os.path.join(ROOT, "paper_1205_6872_gb300", "csrc", "propagate.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_source_sha()
         with open(path) as fh:
             for line in fh:
                 parts = line.split()
@@ -214,6 +224,33 @@ def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None
     algo = 2.0 * tensor_entries(p, half) * entry_bytes(q, precision)  # one read and one write per stored entry
     return dict(ms=ms, launches=launches, clocks=clocks, rho=rho_final, kernel_ms=kern_ms, bytes=algo,
                 kernel_GBps=algo / (kern_ms / 1e3) / 1e9)
+
+
+def time_all_points(q, torch, p, precision, steps, warmup, stream, world, half=True):
+    """rho at every step 0..N (the paper's allPoints): the readout is fused into each of the N steps."""
+    opts = q.quapi_opts_init(precision=precision, cuda_stream=stream, hermitian=int(half))
+    ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, opts)
+    try:
+        grid = list(range(p.N + 1))
+        rho0 = torch.tensor(np.asarray(p.rho0).reshape(-1), dtype=torch.complex128, device="cuda")
+        rho = torch.empty(len(grid) * p.M * p.M, dtype=torch.complex128, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(max(warmup, 1)):
+                q.quapi_propagate_device(ctx, rho0, grid, rho)
+        stream.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            q.quapi_propagate_device(ctx, rho0, grid, rho)
+        e1.record(stream)
+        e1.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        rhos = rho.cpu().numpy().reshape(len(grid), p.M, p.M)
+    finally:
+        q.quapi_destroy(ctx)
+    return dict(ms=ms, rhos=rhos)
 
 
 def time_e2e(q, torch, p, precision, steps, warmup, half=False):
@@ -485,6 +522,12 @@ def main():
         headline_vs_fp64 = float(np.abs(r32h["rho"] - r64f["rho"]).max())
     else:
         headline_vs_fp64 = None
+    rap = time_all_points(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, half=True)
+    forms["fp32_half_all_points"] = dict(
+        value=world * ups / (rap["ms"] / 1000.0), unit=UNIT, ms_per_step=rap["ms"], layout="half",
+        readout=f"allPoints: rho at all {p.N + 1} steps (readout fused into every step)",
+        rho_final_vs_just_final_point=float(np.abs(rap["rhos"][-1] - r32h["rho"]).max()),
+        max_trace_deviation=float(np.abs(np.trace(rap["rhos"], axis1=1, axis2=2) - 1.0).max()))
     if not args.no_batched:
         forms["batched_256_fp32"] = time_batched(q, torch, args.steps, args.warmup, world, rank)
     e2e_s = time_e2e(q, torch, p, q.QUAPI_FP32, args.steps, min(args.warmup, 1), half=True)
@@ -510,12 +553,22 @@ def main():
         rho_final=[[float(z.real), float(z.imag)] for z in r32h["rho"].reshape(-1)],
     )
     if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import clib
         nst = 2
         t = cpu_oracle_sample(p, nst)
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         line["cpu_baseline"] = dict(value=nst * float((p.M * p.M) ** p.L) / t, unit=UNIT, cores=cores,
                                     kind="oracle",
                                     sample=f"{nst} steady-state steps of the 4^14-entry tensor (FP64 oracle)")
+        # the same oracle on one core (one steady-state step)
+        clib.set_threads(1)
+        try:
+            t1 = cpu_oracle_sample(p, 1)
+        finally:
+            clib.set_threads(cores)
+        line["cpu_baseline"]["single_core"] = dict(
+            value=float((p.M * p.M) ** p.L) / t1, unit=UNIT, cores=1,
+            sample="1 steady-state step of the 4^14-entry tensor (FP64 oracle)")
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -53,3 +53,11 @@ def call(name: str, M2: int, n: int, A: np.ndarray, G: np.ndarray, g: np.ndarray
     g = np.ascontiguousarray(g, dtype=np.complex128)
     getattr(lib(), name)(M2, n, _ptr(A), _ptr(G), _ptr(g), _ptr(out))
     return out
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's OpenMP loops from now on (the OpenMP runtime's own setting)."""
+    lib()
+    gomp = ctypes.CDLL("libgomp.so.1")
+    gomp.omp_set_num_threads.argtypes = [ctypes.c_int]
+    gomp.omp_set_num_threads(int(max(1, n)))

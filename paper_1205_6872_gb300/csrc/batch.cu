@@ -30,6 +30,7 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "half_layout.cuh"
@@ -847,13 +848,15 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     return cudaSuccess;
 }
 
+// (M, form, and the sorted (L, N, layout) of the instances): batches with the same signature share a
+// tuned launch shape
 std::string signature(const std::vector<BatchInst>& insts, int M, int form) {
-    std::vector<std::pair<int, int64_t>> v;
-    for (const auto& I : insts) v.emplace_back(I.L, (int64_t)I.N);
+    std::vector<std::tuple<int, int64_t, int>> v;
+    for (const auto& I : insts) v.emplace_back(I.L, (int64_t)I.N, I.herm);
     std::sort(v.begin(), v.end());
     std::ostringstream o;
     o << "M" << M << "f" << form;
-    for (auto& p : v) o << ";" << p.first << "," << p.second;
+    for (auto& p : v) o << ";" << std::get<0>(p) << "," << std::get<1>(p) << (std::get<2>(p) ? "h" : "");
     return o.str();
 }
 
