@@ -199,16 +199,18 @@ template <int M2> __device__ __forceinline__ kahan32 plain_sum(const float2 (&a)
 
 template <int M2>
 __device__ __forceinline__ df2 row_sum(const tf2* __restrict__ isum_row, const df2 (&a)[M2]) {
-    df2 s = tfmul(isum_row[0], a[0]);
+    dfacc acc;
+    acc.init();
 #pragma unroll
-    for (int q = 1; q < M2; ++q) s = dfadd(s, tfmul(isum_row[q], a[q]));
-    return s;
+    for (int q = 0; q < M2; ++q) acc.add_prod(isum_row[q], a[q]);
+    return acc.value();
 }
 template <int M2> __device__ __forceinline__ df2 plain_sum(const df2 (&a)[M2]) {
-    df2 s = a[0];
+    dfacc acc;
+    acc.init();
 #pragma unroll
-    for (int q = 1; q < M2; ++q) s = dfadd(s, a[q]);
-    return s;
+    for (int q = 0; q < M2; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
+    return acc.value();
 }
 
 // hi * (lo * S)

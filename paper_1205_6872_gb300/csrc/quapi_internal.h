@@ -144,6 +144,44 @@ __device__ __forceinline__ df2 tfmul(const tf2& T, const df2& x) {
     return r;
 }
 
+// Running double-float complex sum whose high parts are added with TwoSum and whose low-order
+// terms are collected in plain floats; renormalised once by value().  Adding an exact product
+// (high p, low-order terms e) costs two TwoSums per part instead of a renormalised product
+// followed by a renormalised addition.
+struct dfacc {
+    float sr, er, si, ei;
+    __device__ __forceinline__ void init() { sr = er = si = ei = 0.f; }
+    __device__ __forceinline__ void add_hl(float ph, float pl, float qh, float ql) {  // + (ph + pl) + i (qh + ql)
+        float t;
+        two_sum(sr, ph, sr, t);
+        er += t + pl;
+        two_sum(si, qh, si, t);
+        ei += t + ql;
+    }
+    // + T * x for a triple-float table entry T and a double-float complex x
+    __device__ __forceinline__ void add_prod(const tf2& T, const df2& x) {
+        float pa, ea, pb, eb, pc, ec, pd, ed, t;
+        tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.x, x.l.x, pa, ea);  // Tre * xre
+        tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.y, x.l.y, pb, eb);  // Tim * xim
+        tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.y, x.l.y, pc, ec);  // Tre * xim
+        tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.x, x.l.x, pd, ed);  // Tim * xre
+        two_sum(sr, pa, sr, t);
+        er += t + ea;
+        two_sum(sr, -pb, sr, t);
+        er += t - eb;
+        two_sum(si, pc, si, t);
+        ei += t + ec;
+        two_sum(si, pd, si, t);
+        ei += t + ed;
+    }
+    __device__ __forceinline__ df2 value() const {
+        df2 r;
+        fast_two_sum(sr, er, r.h.x, r.l.x);
+        fast_two_sum(si, ei, r.h.y, r.l.y);
+        return r;
+    }
+};
+
 // x + y for double-float complex values (TwoSum on the high parts)
 __device__ __forceinline__ df2 dfadd(const df2& x, const df2& y) {
     df2 r;
