@@ -164,3 +164,59 @@ def test_half_layout_checkpoint_and_rejections(q):
     with pytest.raises(q.QuapiError) as e:
         q.quapi_setup([-1, 0, 1], np.eye(3), "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 3, q.quapi_opts_init(hermitian=1))
     assert e.value.status == q.QUAPI_ERR_UNSUPPORTED
+
+
+def _random_half_tensor(L, seed, prec):
+    """A random tensor with the Hermitian symmetry, in the device half layout (self-conjugate prefixes
+    get real entries at digits 0 and 3 and conjugate entries at 1 and 2), representable in prec."""
+    Ah = wl.random_tensor(ly.count(L), seed=seed)
+    pref = ly.canonical_order(L - 1)
+    lo_bits = pref & int("01" * (L - 1), 2)
+    hi_bits = (pref & int("10" * (L - 1), 2)) >> 1
+    sc = np.nonzero(lo_bits == hi_bits)[0]  # every digit 0 or 3
+    Ah[4 * sc] = Ah[4 * sc].real
+    Ah[4 * sc + 3] = Ah[4 * sc + 3].real
+    Ah[4 * sc + 2] = np.conj(Ah[4 * sc + 1])
+    return representable(Ah, prec)
+
+
+@pytest.mark.parametrize("prec", [32, 64, 48])
+def test_half_layout_full_size_step_sampled(q, prec):
+    """The headline configuration (memory length 14, steady step, half layout) launched as bench.py
+    times it: sampled outputs of one step, and the full end-point readout, against the oracle."""
+    p = wl.spin_boson_L14()
+    L, n = p.L, p.L + 1
+    eta = oracle.pack_eta(oracle.eta_table(Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, L))
+    etad = oracle.unpack_eta(eta, L)
+    K = oracle.pair_propagator_K(oracle.propagator_U(p.H, p.dt))
+    Ah = _random_half_tensor(L, seed=77, prec=prec)
+    A = ly.from_half(Ah, L)
+    np.testing.assert_array_equal(ly.to_half(A, L), Ah)
+    G, gg, n_in, summed = rec.step_tables(etad, p.s, K, L, n)
+    ctx = q.quapi_setup_eta(p.s, p.H, eta, p.dt, L, q.quapi_opts_init(precision=prec, hermitian=1))
+    try:
+        dA = _to_dev(Ah, prec)
+        dout = _empty_dev(ly.count(L), prec)
+        q.quapi_step_device(ctx, n, dA, dout, None)
+        rho = torch.zeros(4, dtype=torch.complex128, device="cuda")
+        q.quapi_step_device(ctx, L + 3, dA, None, rho)
+        torch.cuda.synchronize()
+        rng = np.random.Generator(np.random.PCG64(9))
+        cnt = ly.count(L)
+        pos = np.concatenate([np.arange(64), cnt - 1 - np.arange(64), rng.integers(0, cnt, 2048)])
+        got = _from_dev(dout[torch.from_numpy(pos).cuda()], prec)
+        got_rho = rho.cpu().numpy()
+    finally:
+        q.quapi_destroy(ctx)
+        del dA
+    full_idx = ly.canonical_indices(L)[pos]
+    want = rec.step_elements(A, G, gg, n_in, summed, full_idx)
+    tol = 2e-6 if prec == 32 else 1e-13
+    assert np.abs(got - want).max() <= tol * (np.abs(want).max() + 1.0)
+    Gr, gr, n_in_r = rec.readout_tables(etad, p.s, K, L, L + 3)
+    want_rho = rec.apply_readout(A, Gr, gr, n_in_r)
+    term = np.sqrt(np.mean(np.abs(A) ** 2))
+    rtol = (1e-6 if prec == 32 else 1e-14) * term * np.sqrt(4 ** (L + 1)) + 1e-12 * np.abs(want_rho).max()
+    assert np.abs(got_rho - want_rho).max() <= rtol, (got_rho, want_rho)
+    # the Hermitian layout's readout is Hermitian by construction
+    assert abs(got_rho[1] - np.conj(got_rho[2])) <= 1e-12 * max(1.0, abs(got_rho[1]))
