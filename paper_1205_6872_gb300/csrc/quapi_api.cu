@@ -244,6 +244,19 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
 
 quapi_status tune_step(quapi_ctx* c);
 
+// Device buffers a function needs only while it runs: freed when it returns, on every path.
+struct DeviceScratch {
+    std::vector<void*> ptrs;
+    template <class T> cudaError_t alloc(T** p, size_t bytes) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+    ~DeviceScratch() {
+        for (void* q : ptrs) cudaFree(q);
+    }
+};
+
 // Allocation, eta (given or by quadrature), propagators and tables.
 quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spectral* J, double beta,
                         const double* eta_host, double dt, int L, const quapi_opts* opts, quapi_ctx** out) {
@@ -339,6 +352,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     SCHECK(cudaMemcpyAsync(c->d_H, H, sizeof(double2) * M * M, cudaMemcpyHostToDevice, c->st), "copy H");
     SCHECK(launch_propagator(c->d_H, M, dt, c->d_U, c->d_K, c->st), "propagator kernel");
 
+    DeviceScratch scratch;  // set-up scratch on the device, freed when set-up returns (also on errors)
     EtaJob* d_jobs = nullptr;
     double* d_gl = nullptr;
     double* d_pan = nullptr;  // tabulated J: panel end points, then J at them
@@ -364,8 +378,8 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         gauss_legendre_nodes(16, gx, gw);
         std::vector<double> gl(gx);
         gl.insert(gl.end(), gw.begin(), gw.end());
-        SCHECK(cudaMalloc(&d_jobs, sizeof(EtaJob) * neta), "cudaMalloc(eta jobs)");
-        SCHECK(cudaMalloc(&d_gl, sizeof(double) * gl.size()), "cudaMalloc(GL nodes)");
+        SCHECK(scratch.alloc(&d_jobs, sizeof(EtaJob) * neta), "cudaMalloc(eta jobs)");
+        SCHECK(scratch.alloc(&d_gl, sizeof(double) * gl.size()), "cudaMalloc(GL nodes)");
         SCHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EtaJob) * neta, cudaMemcpyHostToDevice, c->st), "copy jobs");
         SCHECK(cudaMemcpyAsync(d_gl, gl.data(), sizeof(double) * gl.size(), cudaMemcpyHostToDevice, c->st), "copy GL");
         if (J->kind == QUAPI_J_TABULATED) {
@@ -378,11 +392,8 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
                 const double t1 = J->omega[k], j1 = J->values[k], len = t1 - t0;
                 const double want = std::max(len * kmax / 2.0, 256.0 * len / wmax);
                 const int64_t m = std::max<int64_t>(1, (int64_t)std::ceil(want));
-                if ((int64_t)pw.size() + m > kMaxEtaPanels) {
-                    cudaFree(d_jobs);
-                    cudaFree(d_gl);
+                if ((int64_t)pw.size() + m > kMaxEtaPanels)
                     return bail(fail(c, QUAPI_ERR_ARG, "tabulated J too wide for the eta quadrature panels"));
-                }
                 for (int64_t q = 0; q < m; ++q) {
                     pw.push_back(t0 + len * (double)q / (double)m);
                     pj.push_back(j0 + (j1 - j0) * (double)q / (double)m);
@@ -394,7 +405,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
             pj.push_back(j0);
             const int panels = (int)pw.size() - 1;
             pw.insert(pw.end(), pj.begin(), pj.end());
-            SCHECK(cudaMalloc(&d_pan, sizeof(double) * pw.size()), "cudaMalloc(eta panels)");
+            SCHECK(scratch.alloc(&d_pan, sizeof(double) * pw.size()), "cudaMalloc(eta panels)");
             SCHECK(cudaMemcpyAsync(d_pan, pw.data(), sizeof(double) * pw.size(), cudaMemcpyHostToDevice, c->st),
                    "copy eta panels");
             SCHECK(launch_eta_quadrature_tab(d_jobs, neta, beta, d_pan, d_pan + panels + 1, panels, d_gl, 16,
@@ -442,15 +453,11 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         max_entries = std::max(max_entries, ent);
     }
     BuildDesc* d_descs = nullptr;
-    SCHECK(cudaMalloc(&d_descs, sizeof(BuildDesc) * descs.size()), "cudaMalloc(build descs)");
+    SCHECK(scratch.alloc(&d_descs, sizeof(BuildDesc) * descs.size()), "cudaMalloc(build descs)");
     SCHECK(cudaMemcpyAsync(d_descs, descs.data(), sizeof(BuildDesc) * descs.size(), cudaMemcpyHostToDevice, c->st),
            "copy build descs");
     SCHECK(launch_build_tables(d_descs, (int)descs.size(), M2, max_entries, c->st), "table build kernel");
     SCHECK(cudaStreamSynchronize(c->st), "setup synchronize");
-    cudaFree(d_descs);
-    if (d_jobs) cudaFree(d_jobs);
-    if (d_gl) cudaFree(d_gl);
-    if (d_pan) cudaFree(d_pan);
     if (c->tune) {
         quapi_status ts = tune_step(c);
         if (ts != QUAPI_OK) return bail(ts);
