@@ -147,12 +147,14 @@ template <> struct RhoAcc<QUAPI_FP64> {
     double2 s;
     __device__ __forceinline__ void init() { s = make_double2(0.0, 0.0); }
     __device__ __forceinline__ void add(double2 v) { s = cadd(s, v); }
+    __device__ __forceinline__ void add_re(double2 v, double k) { s.x += k * v.x; }  // + k Re(v)
     __device__ __forceinline__ double2 value() const { return s; }
 };
 template <> struct RhoAcc<QUAPI_FP32> {
     cacc32 a;
     __device__ __forceinline__ void init() { a.init(make_float2(0.f, 0.f)); }
     __device__ __forceinline__ void add(float2 v) { a.add(v); }
+    __device__ __forceinline__ void add_re(float2 v, float k) { a.add_real(k * v.x); }  // k = 1 or 2: exact
     __device__ __forceinline__ double2 value() const {
         return make_double2((double)a.s.x + (double)a.c.x, (double)a.s.y + (double)a.c.y);
     }
@@ -162,6 +164,12 @@ template <> struct RhoAcc<QUAPI_DF64> {
     df2 a;
     __device__ __forceinline__ void init() { a.h = a.l = make_float2(0.f, 0.f); }
     __device__ __forceinline__ void add(df2 v) { a = dfadd(a, v); }
+    __device__ __forceinline__ void add_re(const df2& v, float k) {  // + k Re(v), k = 1 or 2 (exact scaling)
+        float s, t;
+        two_sum(a.h.x, k * v.h.x, s, t);
+        t += a.l.x + k * v.l.x;
+        fast_two_sum(s, t, a.h.x, a.l.x);
+    }
     __device__ __forceinline__ double2 value() const {
         return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
     }
@@ -709,11 +717,11 @@ __device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const t
             Elem rb[4];
             herm_rows<FORM, DIAG, true, true>(T, b, fb, rb);
             racc[1].add(rb[1]);
-            racc[0].add(twice_real(r[0]));
-            racc[3].add(twice_real(r[3]));
+            racc[0].add_re(r[0], 2);  // rows 0 and 3: the conjugate partner adds the conjugate
+            racc[3].add_re(r[3], 2);
         } else {
-            racc[0].add(real_part(r[0]));
-            racc[3].add(real_part(r[3]));
+            racc[0].add_re(r[0], 1);
+            racc[3].add_re(r[3], 1);
         }
     }
 }
@@ -726,9 +734,10 @@ constexpr uint32_t kChunk = 256;
 
 // Minimum resident CTAs per SM given to the compiler (a register cap).  Measured at memory length 14:
 // the FP32 step runs best at 8 CTAs (32 registers; 0.370 ms against 0.380 ms at 6 CTAs and
-// 0.425 ms uncapped); kernels with the readout, and the DF64 and FP64 forms, at 3-4.
+// 0.425 ms uncapped), the FP32 step with the readout at 3 (0.687 ms against 0.725 ms at 4);
+// the readout alone, and the DF64 and FP64 forms, at 3-4.
 template <int FORM, bool WRITE, bool READ> constexpr int herm_min_ctas() {
-    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 8 : 4;
+    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 8 : (WRITE ? 3 : 4);
     if (WRITE && READ) return 3;
     return (FORM == QUAPI_DF64 && READ) ? 3 : 4;
 }

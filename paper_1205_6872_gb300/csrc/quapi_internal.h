@@ -73,6 +73,12 @@ struct cacc32 {
         c.x += ex;
         c.y += ey;
     }
+    __device__ __forceinline__ void add_real(float x) {  // + x (real)
+        float sx, ex;
+        two_sum(s.x, x, sx, ex);
+        s.x = sx;
+        c.x += ex;
+    }
 };
 
 // Kahan-compensated complex sum for the short sums over the summed path index
