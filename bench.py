@@ -276,6 +276,26 @@ def batch_updates(probs):
     return float(sum((p.M * p.M) ** p.L * max(p.N - p.L + 1, 0) for p in probs))
 
 
+def batch_hbm_bytes(probs, half, entry_bytes=8, resident_bytes=32 * 1024):
+    """Algorithmic HBM bytes of one batched run: one read and one write of every stored entry at every
+    step (growth and the final readout included) of each instance too large to stay in shared memory."""
+    from paper_1205_6872_gb300 import layout as ly
+    total = 0
+    for p in probs:
+        M2 = p.M * p.M
+        if 2 * M2 ** p.L * entry_bytes <= resident_bytes:
+            continue
+        stored = (lambda n: ly.count(n)) if half else (lambda n: M2 ** n)
+        for n in range(1, p.N + 1):
+            if n < p.L and n < p.N:
+                total += (stored(n) + stored(n + 1)) * entry_bytes
+            elif n < p.N:
+                total += 2 * stored(p.L) * entry_bytes
+            else:
+                total += stored(min(n, p.L)) * entry_bytes
+    return float(total)
+
+
 def time_batched(q, torch, steps, warmup, world, rank):
     """256 spin-boson instances: one batched FP32 launch (autotuned, graph replay), with the tiled
     instances in the Hermitian half layout and in the full layout, vs the same instances solved one
@@ -324,12 +344,16 @@ def time_batched(q, torch, steps, warmup, world, rank):
             q.quapi_destroy(c)
     diff = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32[h], r64))) for h in (0, 1)}
     total = replicas.reduce_sum(ups)
+    peak, _ = measured_peaks()
+    gbps = {h: replicas.reduce_sum(batch_hbm_bytes(probs, h == 1)) / batched_s[h] / 1e9 for h in (0, 1)}
     return dict(workload="batched_256", instances=len(allp), layout="half (tiled instances)",
                 value=total / batched_s[1], unit=UNIT, ms_per_batch=1000.0 * batched_s[1],
                 full_layout_value=total / batched_s[0], full_layout_ms_per_batch=1000.0 * batched_s[0],
                 sequential_fp64_ms=1000.0 * seq_s, sequential_fp64_value=total / seq_s,
                 speedup_vs_sequential_fp64=seq_s / batched_s[1], fp32_vs_fp64_max_abs=diff[1],
-                fp32_full_vs_fp64_max_abs=diff[0])
+                fp32_full_vs_fp64_max_abs=diff[0],
+                algorithmic_GBps=gbps[1], frac_of_hbm=gbps[1] / peak,
+                full_layout_algorithmic_GBps=gbps[0], full_layout_frac_of_hbm=gbps[0] / peak)
 
 
 def cpu_oracle_sample(p, nsteps):
