@@ -198,31 +198,16 @@ __device__ __forceinline__ void herm_rows_b(const OpTabs<2, FORM>& T, bool diag,
     o[1] = tab_mul(ldt(T.hi + T.hi_size + fh), tab_mul2(ldt(T.lo + T.lo_size + fl), s, c));
 }
 
-// Decode of position c (np digits) for one lane of a warp whose 32 lanes take the consecutive
-// positions c0 .. c0 + 31 (c = c0 + lane): when the 32 stay in one digit-1 block of level >= 2 the
-// warp decodes c0 once, otherwise each lane decodes its own position.
-__device__ __forceinline__ void herm_decode_warp(uint32_t c0, uint32_t lane, int np, uint32_t& f, bool& sc,
-                                                 uint32_t& h, bool& shc) {
-    uint32_t f0, h0;
-    bool sc0, shc0;
-    half_decode_pair(c0, np, f0, sc0, h0, shc0);
-    const uint32_t t = (f0 ^ (f0 >> 1)) & 0x55555555u;
-    const uint32_t r1 = t ? (1u << (31 - __clz(t))) : 0u;
-    if (!sc0 && !shc0 && (f0 & 3u) == 0u && (f0 & (r1 - 1u)) + 32u <= r1) {
-        f = f0 + lane;
-        h = h0 + (lane >> 2);
-        sc = false;
-        shc = false;
-    } else {
-        half_decode_pair(c0 + lane, np, f, sc, h, shc);
-    }
-}
-
-// Steady step: positions c = base + u * kBThreads + threadIdx.x of the np-digit canonical prefixes.
+// Steady step over the tile's positions [tile_base, tile_base + kBThreads * FPT): warp w takes the
+// 32 * FPT consecutive positions from tile_base + w * 32 * FPT, lane l the positions l, l + 32, ...
+// of that chunk.  A chunk inside one digit-1 block of level >= 2 is decoded once per warp (its
+// prefixes are then consecutive plain indices f = f0 + i with fiber positions h0 + i / 4);
+// otherwise each position is decoded on its own.
 template <int FORM, int FPT>
 __device__ void herm_step_tile(const OpRef& op, const void* in, void* outv, int np, int64_t tile_base) {
     using Elem = typename Form<FORM>::Elem;
     constexpr int remap[4] = {0, 2, 1, 3};
+    constexpr uint32_t kWarpChunk = 32u * FPT;
     const OpTabs<2, FORM> T = tabs_of<2, FORM>(op);
     const Elem* A = reinterpret_cast<const Elem*>(in);
     Elem* out = reinterpret_cast<Elem*>(outv);
@@ -230,15 +215,28 @@ __device__ void herm_step_tile(const OpRef& op, const void* in, void* outv, int 
     const uint32_t top = (np >= 1) ? (1u << (2 * (np - 1))) : 0u;
     const uint32_t cnh = (np >= 1) ? half_count32(np - 1) : 0u;
     const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t cb = (uint32_t)tile_base + (threadIdx.x >> 5) * kWarpChunk;
+    if (cb >= npre) return;
+    uint32_t f0, h0;
+    bool sc0, shc0;
+    half_decode_pair(cb, np, f0, sc0, h0, shc0);
+    const uint32_t t = (f0 ^ (f0 >> 1)) & 0x55555555u;
+    const uint32_t r1 = t ? (1u << (31 - __clz(t))) : 0u;
+    const bool fast = !sc0 && !shc0 && (f0 & 3u) == 0u && (f0 & (r1 - 1u)) + kWarpChunk <= r1;
 #pragma unroll 1
-    for (int u = 0; u < FPT; ++u) {
-        const uint32_t c0 = (uint32_t)tile_base + u * kBThreads + (threadIdx.x & ~31u);
-        if (c0 >= npre) break;
-        const uint32_t c = c0 + lane;
-        uint32_t f = 0, h = 0;
-        bool sc = true, shc = true;
-        herm_decode_warp(c0, lane, np, f, sc, h, shc);  // warp-uniform call: every lane takes part
-        if (c >= npre) continue;
+    for (uint32_t i = lane; i < kWarpChunk; i += 32) {
+        const uint32_t c = cb + i;
+        if (c >= npre) break;
+        uint32_t f, h;
+        bool sc, shc;
+        if (fast) {
+            f = f0 + i;
+            h = h0 + (i >> 2);
+            sc = false;
+            shc = false;
+        } else {
+            half_decode_pair(c, np, f, sc, h, shc);
+        }
         Elem a[4], o[4];
         ld_fiber4<FORM>(A, c, a);
         herm_rows_b<FORM, false>(T, op.diag != 0, a, f, o);
