@@ -8,8 +8,10 @@
 // growth entries).  Items are numbered resident first, then step-major
 // (wave n = step n of every instance), so an item only ever depends on items
 // with smaller numbers: a CTA takes the next number from an atomic counter,
-// waits (bounded) until its instance has completed every tile of the previous
-// step, processes its tiles, and publishes the count.  The readout at the
+// looks up its (step, instance, first tile) in a flat item table, waits
+// (bounded) until its instance has completed every tile of the previous step,
+// takes the number of its following item (the atomic's latency then overlaps
+// the tiles), processes its tiles, and publishes the count.  The readout at the
 // instance's final step writes one partial sum per tile; the CTA finishing the
 // last tile adds them in tile order (deterministic result).
 //
@@ -53,9 +55,9 @@ struct BatchArgs {
     int ntiled;
     int nwaves;                 // largest final step among the tiled instances
     const int64_t* wave_off;    // [nwaves + 2]: first item of wave n (wave 0 = resident items)
-    const int64_t* inst_off;    // [(nwaves + 1) x (ntiled + 1)]: item offset of tiled instance k in wave n
     const unsigned* need;       // [(nwaves + 1) x ntiled]: tiles instance k completes before step n
     const unsigned* ntiles;     // [(nwaves + 1) x ntiled]: tiles of instance k at step n (0: none)
+    const uint4* items;         // [total_items - nresident]: (step n, tiled instance k, first tile, 0)
     int64_t total_items;
     unsigned long long* next_item;
     int* err;
@@ -409,38 +411,28 @@ __global__ void __launch_bounds__(kBThreads, HO ? 4 : ((M == 2) ? 3 : 1)) batch_
     __shared__ int s_stop;
     __shared__ double2 red[kBThreads / 32][M2];
 
+    // the next item's number is taken while the current one runs (thread 0, after its dependency wait)
+    if (threadIdx.x == 0) {
+        const int e = *reinterpret_cast<volatile int*>(args.err);
+        s_item = e ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
+    }
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int e = *reinterpret_cast<volatile int*>(args.err);
-            s_item = e ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
-        }
-        __syncthreads();
         const long long g = s_item;
-        __syncthreads();
+        __syncthreads();  // every thread holds g before thread 0 writes the next number
         if (g < 0 || g >= args.total_items) break;
         if (g < args.wave_off[1]) {
-            run_resident<M, FORM>(args.inst[args.resident[g]], smem, red);
+            if (threadIdx.x == 0) {
+                const int e = *reinterpret_cast<volatile int*>(args.err);
+                s_item = e ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
+            }
+            run_resident<M, FORM>(args.inst[args.resident[g]], smem, red);  // ends with a barrier
             continue;
         }
-        // wave (step) n: largest n with wave_off[n] <= g
-        int lo = 1, hi = args.nwaves;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (args.wave_off[mid] <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        const int n = lo;
-        const int64_t r = g - args.wave_off[n];
-        const int64_t* io = args.inst_off + (int64_t)n * (args.ntiled + 1);
-        int kl = 0, kh = args.ntiled - 1;
-        while (kl < kh) {
-            const int mid = (kl + kh + 1) >> 1;
-            if (io[mid] <= r) kl = mid;
-            else kh = mid - 1;
-        }
-        const int k = kl;
+        const uint4 d = args.items[g - args.wave_off[1]];
+        const int n = (int)d.x, k = (int)d.y;
         const unsigned nt = args.ntiles[(int64_t)n * args.ntiled + k];
-        const unsigned t0 = (unsigned)(r - io[k]) * (unsigned)args.group;
+        const unsigned t0 = d.z;
         const unsigned t1 = min(t0 + (unsigned)args.group, nt);
         const BatchInst& I = args.inst[args.tiled[k]];
 
@@ -465,6 +457,8 @@ __global__ void __launch_bounds__(kBThreads, HO ? 4 : ((M == 2) ? 3 : 1)) batch_
             }
             __threadfence();
             s_stop = stop;
+            const int e = *reinterpret_cast<volatile int*>(args.err);
+            s_item = (stop || e) ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
         }
         __syncthreads();
         if (s_stop) break;
@@ -629,7 +623,7 @@ struct Plan {
     int64_t total_items = 0;
     int grid = 0;
     size_t smem = 0;
-    DevBuf d_inst, d_res, d_tiled, d_wave, d_ioff, d_need, d_nt, d_next, d_err, d_cnt, d_part, d_rho0, d_rho;
+    DevBuf d_inst, d_res, d_tiled, d_wave, d_items, d_need, d_nt, d_next, d_err, d_cnt, d_part, d_rho0, d_rho;
     double* h_rho0 = nullptr;  // pinned staging
     double* h_rho = nullptr;
     BatchArgs args{};
@@ -795,7 +789,8 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     for (int i : P.tiled) nw = std::max<int>(nw, P.inst[i].N);
     P.nwaves = nw;
     const int nt = (int)P.tiled.size();
-    std::vector<int64_t> wave_off(nw + 2, 0), ioff((size_t)(nw + 1) * (nt + 1), 0);
+    std::vector<int64_t> wave_off(nw + 2, 0);
+    std::vector<uint4> items;  // tiled items in work-list order
     std::vector<unsigned> need((size_t)(nw + 1) * std::max(nt, 1), 0), ntl((size_t)(nw + 1) * std::max(nt, 1), 0);
     wave_off[0] = 0;
     wave_off[1] = (int64_t)P.resident.size();
@@ -807,11 +802,10 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
             const unsigned t = tiles_at(M2, I.L, I.N, n, te, I.read.n_in, I.herm != 0);
             ntl[(size_t)n * nt + k] = t;
             need[(size_t)n * nt + k] = cum[k];
-            ioff[(size_t)n * (nt + 1) + k] = acc;
+            for (unsigned t0 = 0; t0 < t; t0 += (unsigned)group) items.push_back(make_uint4((unsigned)n, (unsigned)k, t0, 0u));
             acc += (t + group - 1) / group;
             cum[k] += t;
         }
-        ioff[(size_t)n * (nt + 1) + nt] = acc;
         wave_off[n + 1] = wave_off[n] + acc;
     }
     P.total_items = wave_off[nw + 1];
@@ -824,7 +818,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     if ((e = upload(P.d_res, P.resident)) != cudaSuccess) return e;
     if ((e = upload(P.d_tiled, P.tiled)) != cudaSuccess) return e;
     if ((e = upload(P.d_wave, wave_off)) != cudaSuccess) return e;
-    if ((e = upload(P.d_ioff, ioff)) != cudaSuccess) return e;
+    if ((e = upload(P.d_items, items)) != cudaSuccess) return e;
     if ((e = upload(P.d_need, need)) != cudaSuccess) return e;
     if ((e = upload(P.d_nt, ntl)) != cudaSuccess) return e;
     BatchArgs& a = P.args;
@@ -835,7 +829,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     a.ntiled = nt;
     a.nwaves = nw;
     a.wave_off = static_cast<const int64_t*>(P.d_wave.p);
-    a.inst_off = static_cast<const int64_t*>(P.d_ioff.p);
+    a.items = static_cast<const uint4*>(P.d_items.p);
     a.need = static_cast<const unsigned*>(P.d_need.p);
     a.ntiles = static_cast<const unsigned*>(P.d_nt.p);
     a.total_items = P.total_items;
