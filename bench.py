@@ -298,8 +298,9 @@ def batch_hbm_bytes(probs, half, entry_bytes=8, resident_bytes=32 * 1024):
 
 def time_batched(q, torch, steps, warmup, world, rank):
     """256 spin-boson instances: one batched FP32 launch (autotuned, graph replay), with the tiled
-    instances in the Hermitian half layout and in the full layout, vs the same instances solved one
-    after another with the plain FP64 propagator.  Under N ranks each rank takes a contiguous shard
+    instances in the Hermitian half layout and in the full layout, and one DF64 (FP64-equivalent)
+    launch in the half layout, vs the same instances solved one after another with the plain FP64
+    propagator.  Under N ranks each rank takes a contiguous shard
     of the instances."""
     from paper_1205_6872_gb300 import replicas
     from paper_1205_6872_gb300 import workloads as wl
@@ -310,9 +311,11 @@ def time_batched(q, torch, steps, warmup, world, rank):
     rho0s = [p.rho0 for p in probs]
     Ns = [p.N for p in probs]
     batched_s, r32 = {}, {}
-    for half in (1, 0):
+    # keys: 1 = FP32 half layout, 0 = FP32 full layout, 2 = DF64 (FP64-equivalent) half layout
+    for half in (1, 0, 2):
+        prec = q.QUAPI_DF64 if half == 2 else q.QUAPI_FP32
         c32 = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
-                             q.quapi_opts_init(precision=q.QUAPI_FP32, tune=1, hermitian=half)) for p in probs]
+                             q.quapi_opts_init(precision=prec, tune=1, hermitian=int(half != 0))) for p in probs]
         try:
             for _ in range(max(warmup, 1)):
                 q.quapi_propagate_batch(c32, rho0s, Ns)  # first call tunes and captures the graph
@@ -342,7 +345,7 @@ def time_batched(q, torch, steps, warmup, world, rank):
     finally:
         for c in c64:
             q.quapi_destroy(c)
-    diff = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32[h], r64))) for h in (0, 1)}
+    diff = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32[h], r64))) for h in (0, 1, 2)}
     total = replicas.reduce_sum(ups)
     peak, _ = measured_peaks()
     gbps = {h: replicas.reduce_sum(batch_hbm_bytes(probs, h == 1)) / batched_s[h] / 1e9 for h in (0, 1)}
@@ -353,7 +356,9 @@ def time_batched(q, torch, steps, warmup, world, rank):
                 speedup_vs_sequential_fp64=seq_s / batched_s[1], fp32_vs_fp64_max_abs=diff[1],
                 fp32_full_vs_fp64_max_abs=diff[0],
                 algorithmic_GBps=gbps[1], frac_of_hbm=gbps[1] / peak,
-                full_layout_algorithmic_GBps=gbps[0], full_layout_frac_of_hbm=gbps[0] / peak)
+                full_layout_algorithmic_GBps=gbps[0], full_layout_frac_of_hbm=gbps[0] / peak,
+                df64_half_value=total / batched_s[2], df64_half_ms_per_batch=1000.0 * batched_s[2],
+                df64_half_speedup_vs_sequential_fp64=seq_s / batched_s[2], df64_half_vs_fp64_max_abs=diff[2])
 
 
 def cpu_oracle_sample(p, nsteps):
@@ -444,15 +449,16 @@ def run_kernel_only(args):
 
 
 def run_batched_only(args):
-    """One batched FP32 launch over --batch-n seeded spin-boson instances (3 warm-up runs, then
-    --reps timed runs), optionally in the half layout and autotuned.  Used for ncu captures of the
+    """One batched launch (form --form) over --batch-n seeded spin-boson instances (3 warm-up runs,
+    then --reps timed runs), optionally in the half layout and autotuned.  Used for ncu captures of the
     batched kernel on a small case."""
     import torch
     from paper_1205_6872_gb300 import quapi as q
     from paper_1205_6872_gb300 import workloads as wl
     torch.cuda.set_device(0)
     probs = wl.batched_256(n=args.batch_n, N=args.batch_steps)
-    opts = q.quapi_opts_init(precision=q.QUAPI_FP32, tune=int(args.tune), hermitian=int(args.hermitian))
+    prec = {"fp32": q.QUAPI_FP32, "fp64": q.QUAPI_FP64, "df64": q.QUAPI_DF64}[args.form]
+    opts = q.quapi_opts_init(precision=prec, tune=int(args.tune), hermitian=int(args.hermitian))
     ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L, opts) for p in probs]
     try:
         rho0s, Ns = [p.rho0 for p in probs], [p.N for p in probs]
@@ -466,7 +472,8 @@ def run_batched_only(args):
     finally:
         for c in ctxs:
             q.quapi_destroy(c)
-    print(json.dumps(dict(mode="batched-only", instances=len(probs), N=args.batch_steps, hermitian=bool(args.hermitian),
+    print(json.dumps(dict(mode="batched-only", form=args.form, instances=len(probs), N=args.batch_steps,
+                          hermitian=bool(args.hermitian),
                           tune=bool(args.tune), ms_per_batch=ms,
                           value=batch_updates(probs) / (ms / 1e3), unit=UNIT)))
     return 0
@@ -484,7 +491,8 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused steady-state step kernel (profiling case)")
     ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
-    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"], help="form for --kernel-only")
+    ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"],
+                    help="form for --kernel-only / --batched-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
     ap.add_argument("--hermitian", action="store_true", help="--kernel-only / --batched-only: Hermitian half layout")
     ap.add_argument("--tune", action="store_true", help="--batched-only: autotune the launch shape")

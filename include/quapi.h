@@ -201,14 +201,18 @@ quapi_status quapi_propagate_resume(quapi_ctx* c, const int64_t* steps, int nste
 quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, void* A_out_dev,
                                void* rho_dev);
 
-/* Batched propagation of n independent contexts (all FP32 or all FP64, M = 2)
- * to their own final steps, in one persistent, CUDA-graph-captured launch.
- *   ctxs[i]        contexts from quapi_setup / quapi_setup_eta (same precision)
- *   rho0s[i]       [M*M] complex (host)
+/* Batched propagation of n independent contexts (one precision and one M for
+ * all: FP64, FP32 or DF64; M = 2 or 3; each context in its own layout) to
+ * their own final steps, in one persistent, CUDA-graph-captured launch.  The
+ * library has no counterpart in the paper (which sweeps parameters one run at
+ * a time); each instance's result equals its quapi_propagate result.
+ *   ctxs[i]        contexts from quapi_setup / quapi_setup_eta (same precision, same M)
+ *   rho0s[i]       [M*M] complex (host); Hermitian for a half-layout context
  *   nsteps_each[i] final step N_i >= 0
  *   rho_final[i]   [M*M] complex (host, caller-owned): rho(t_{N_i})
  * Work runs on ctxs[0]'s stream.  Blocks until all results are written.
- * Errors: QUAPI_ERR_ARG, QUAPI_ERR_UNSUPPORTED (mixed precision or M),
+ * Errors: QUAPI_ERR_ARG (NULL arrays, a context twice, N_i < 0, non-Hermitian
+ * rho0 for a half-layout context), QUAPI_ERR_UNSUPPORTED (mixed precision or M),
  * QUAPI_ERR_TIMEOUT (a device-side dependency wait gave up), QUAPI_ERR_CUDA. */
 quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
                                    const int64_t* nsteps_each, double* const* rho_final);

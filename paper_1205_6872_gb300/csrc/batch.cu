@@ -90,9 +90,22 @@ template <> __device__ __forceinline__ double2 from_d<QUAPI_FP64>(double2 v) { r
 template <> __device__ __forceinline__ float2 from_d<QUAPI_FP32>(double2 v) {
     return make_float2((float)v.x, (float)v.y);
 }
+template <> __device__ __forceinline__ df2 from_d<QUAPI_DF64>(double2 v) {  // hi = RN32(v), lo = RN32(v - hi)
+    df2 r;
+    r.h = make_float2((float)v.x, (float)v.y);
+    r.l = make_float2((float)(v.x - (double)r.h.x), (float)(v.y - (double)r.h.y));
+    return r;
+}
 
 __device__ __forceinline__ double2 ld_l2(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ld_l2(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ df2 ld_l2(const df2* p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    df2 r;
+    r.h = make_float2(v.x, v.y);
+    r.l = make_float2(v.z, v.w);
+    return r;
+}
 
 __device__ double2 initial_entry(const BatchInst& I, int M, int x, const double2* rho0) {
     const double sp = I.s[x / M], sm = I.s[x % M], d = sp - sm;
@@ -117,6 +130,14 @@ template <> struct Acc<QUAPI_FP32> {
     __device__ void init() { a.init(make_float2(0.f, 0.f)); }
     __device__ void add(float2 v) { a.add(v); }
     __device__ double2 value() const { return make_double2((double)a.s.x + a.c.x, (double)a.s.y + a.c.y); }
+};
+template <> struct Acc<QUAPI_DF64> {
+    df2 a;
+    __device__ void init() { a.h = a.l = make_float2(0.f, 0.f); }
+    __device__ void add(const df2& v) { a = dfadd(a, v); }
+    __device__ double2 value() const {
+        return make_double2((double)a.h.x + (double)a.l.x, (double)a.h.y + (double)a.l.y);
+    }
 };
 
 // Block-wide sum of acc (one value per row) in a fixed order; the result is
@@ -400,9 +421,10 @@ __device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*
 
 // HO: every tiled instance of the batch is in the Hermitian half layout (M = 2); the full-layout tile
 // code is left out, which lowers the register need: 4 resident CTAs per SM (256 instances, FP32:
-// 82 ms per batch against 87 ms at 3 CTAs and 91 ms at 5), the general kernel 3.
+// 82 ms per batch against 87 ms at 3 CTAs and 91 ms at 5), the general kernel 3; the DF64 form 2.
 template <int M, int FORM, int FPT, bool HO>
-__global__ void __launch_bounds__(kBThreads, HO ? 4 : ((M == 2) ? 3 : 1)) batch_kernel(BatchArgs args) {
+__global__ void __launch_bounds__(kBThreads, FORM == QUAPI_DF64 ? 2 : (HO ? 4 : ((M == 2) ? 3 : 1)))
+    batch_kernel(BatchArgs args) {
     constexpr int M2 = M * M;
     using Elem = typename Form<FORM>::Elem;
     constexpr int TE = kBThreads * FPT;  // fibers (or growth entries) per tile
@@ -707,6 +729,8 @@ cudaError_t launch_plan(Plan& P, cudaStream_t st, bool prep = false) {
     if (P.M == 2 && P.form == QUAPI_FP64) return launch_batch_fpt<2, QUAPI_FP64>(P, st, prep);
     if (P.M == 3 && P.form == QUAPI_FP32) return launch_batch_fpt<3, QUAPI_FP32>(P, st, prep);
     if (P.M == 3 && P.form == QUAPI_FP64) return launch_batch_fpt<3, QUAPI_FP64>(P, st, prep);
+    if (P.M == 2 && P.form == QUAPI_DF64) return launch_batch_fpt<2, QUAPI_DF64>(P, st, prep);
+    if (P.M == 3 && P.form == QUAPI_DF64) return launch_batch_fpt<3, QUAPI_DF64>(P, st, prep);
     return cudaErrorInvalidValue;
 }
 
@@ -734,7 +758,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
                        uint64_t wait_ns) {
     cudaError_t e;
     const int M2 = M * M;
-    const size_t elt = form == QUAPI_FP64 ? 16 : 8;
+    const size_t elt = form == QUAPI_FP32 ? 8 : 16;  // complex float; complex double or double-float pair
     P.M = M;
     P.form = form;
     P.fpt = fpt;
@@ -939,8 +963,6 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
-        if (form == QUAPI_DF64)
-            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED, "batch: the double-float form runs one context at a time");
         if (ctx_half_layout(ctxs[i])) {  // the half layout stores one of each conjugate pair: rho0 = rho0^dagger
             const double* r0 = rho0s[i];
             for (int r = 0; r < M; ++r)

@@ -22,6 +22,10 @@ template <> struct Form<QUAPI_FP32> {
     using Elem = float2;
     using Tab = ff2;
 };
+template <> struct Form<QUAPI_DF64> {
+    using Elem = df2;
+    using Tab = tf2;
+};
 
 template <int M> __host__ __device__ constexpr bool diag_point(int x) { return (x / M) == (x % M); }
 
@@ -56,8 +60,20 @@ __device__ __forceinline__ ff2 ldt(const ff2* p) {
     return t;
 }
 
+__device__ __forceinline__ tf2 ldt(const tf2* p) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    tf2 t;
+    t.t1 = make_float2(a.x, a.y);
+    t.t2 = make_float2(a.z, a.w);
+    t.t3 = make_float2(b.x, b.y);
+    t.pad = make_float2(0.f, 0.f);
+    return t;
+}
+
 __device__ __forceinline__ double2 tab_mul(const double2& T, double2 v) { return cmul(T, v); }
 __device__ __forceinline__ float2 tab_mul(const ff2& T, float2 v) { return ffmul(T, v); }
+__device__ __forceinline__ df2 tab_mul(const tf2& T, const df2& v) { return tfmul(T, v); }
 
 // sum_old isum[old] * a[old]: FP64 plain, FP32 Kahan-compensated (value = s + c)
 template <int M2>
@@ -76,6 +92,24 @@ __device__ __forceinline__ float2 tab_dot(const ff2* __restrict__ row, const flo
     for (int q = 1; q < M2; ++q) k.add(ffmul(ldt(row + q), a[q]));
     c = k.c;
     return k.s;
+}
+// DF64: exact products added with TwoSum, renormalised once (c stays zero: the value is the pair)
+template <int M2>
+__device__ __forceinline__ df2 tab_dot(const tf2* __restrict__ row, const df2 (&a)[M2], df2& c) {
+    dfacc acc;
+    acc.init();
+#pragma unroll
+    for (int q = 0; q < M2; ++q) acc.add_prod(ldt(row + q), a[q]);
+    c = df2{};
+    return acc.value();
+}
+template <int M2> __device__ __forceinline__ df2 plain_dot(const df2 (&a)[M2], df2& c) {
+    dfacc acc;
+    acc.init();
+#pragma unroll
+    for (int q = 0; q < M2; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
+    c = df2{};
+    return acc.value();
 }
 template <int M2> __device__ __forceinline__ double2 plain_dot(const double2 (&a)[M2], double2& c) {
     double2 s = a[0];
@@ -96,6 +130,7 @@ template <int M2> __device__ __forceinline__ float2 plain_dot(const float2 (&a)[
 // table * (s + c)
 __device__ __forceinline__ double2 tab_mul2(const double2& T, double2 s, double2 /*c*/) { return cmul(T, s); }
 __device__ __forceinline__ float2 tab_mul2(const ff2& T, float2 s, float2 c) { return ffmul2(T, s, c); }
+__device__ __forceinline__ df2 tab_mul2(const tf2& T, const df2& s, const df2& /*c*/) { return tfmul(T, s); }
 
 // All M2 outputs of fiber f (a = its M2 entries).  DIAG: diagonal rows use the
 // plain sum and skip lo (valid when K sits in hi and isum has no K).

@@ -36,7 +36,7 @@ def _ctxs(q, probs, prec, tune=0, hermitian=0):
 
 
 @pytest.mark.parametrize("half", [0, 1])
-@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5), (48, 1e-12)])
 def test_batched_256_against_stored_oracle(q, prec, tol, half):
     """half = 1: the tiled instances keep their tensors in the Hermitian half layout."""
     probs = wl.batched_256()
@@ -55,7 +55,7 @@ def test_batched_256_against_stored_oracle(q, prec, tol, half):
 
 
 @pytest.mark.parametrize("half", [0, 1])
-@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5)])
+@pytest.mark.parametrize("prec,tol", [(64, 1e-12), (32, 1e-5), (48, 1e-12)])
 def test_batched_mixed_final_steps(q, prec, tol, half):
     """Final steps 0, 1, below and above L, several memory lengths, M = 2 (readouts in the growth phase too)."""
     base = wl.batched_256(n=12, seed=3)
@@ -90,6 +90,26 @@ def test_batched_half_and_full_layouts_together(q):
     for p, N, r in zip(probs, Ns, got):
         want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, [N])[N]
         assert np.abs(r - want).max() <= 1e-12, (p.L, N)
+
+
+def test_batched_three_level_df64(q):
+    """M = 3 in the DF64 form (FP64-equivalent on the FP32 pipes) against the oracle."""
+    probs = []
+    for i, L in enumerate([2, 3, 4, 5]):
+        p = wl.three_level_L8()
+        p.L = L
+        p.H = wl.random_hermitian(3, 60 + i)
+        probs.append(p)
+    Ns = [7, 3, 12, 9]
+    ctxs = _ctxs(q, probs, 48)
+    try:
+        got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], Ns, M=3)
+    finally:
+        for c in ctxs:
+            q.quapi_destroy(c)
+    for p, N, r in zip(probs, Ns, got):
+        want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, [N])[N]
+        assert np.abs(r - want).max() <= 1e-12
 
 
 def test_batched_three_level(q):
