@@ -222,9 +222,6 @@ template <int M2> __device__ __forceinline__ df2 plain_sum(const df2 (&a)[M2]) {
 }
 
 // hi * (lo * S)
-__device__ __forceinline__ double2 apply_p(const double2& hi, const double2& lo, double2 S) {
-    return cmul(hi, cmul(lo, S));
-}
 __device__ __forceinline__ float2 apply_p(const ff2& hi, const ff2& lo, const kahan32& S) {
     return ffmul(hi, ffmul2(lo, S.s, S.c));
 }

@@ -158,15 +158,6 @@ OpPlan plan_readout(int M, int L, int64_t N, int endpoint) {
     return make_plan(M, OP_READ, n_in, true, idx, self);
 }
 
-size_t plan_bytes(const OpPlan& p, int M2, int form) {
-    const size_t e = table_entry_bytes(form);
-    size_t b = 0;
-    if (p.summed) b += (size_t)M2 * M2 * e;
-    b += (size_t)M2 * p.lo_size * e;
-    b += (size_t)M2 * p.hi_size * e;
-    return b;
-}
-
 void assign_offsets(OpPlan& p, int M2, int form, size_t& cursor) {
     const size_t e = table_entry_bytes(form);
     auto align = [](size_t v) { return (v + 255) & ~(size_t)255; };
