@@ -93,7 +93,8 @@ typedef struct {
     int endpoint_mode;      /* QUAPI_ENDPOINT_STRANG (default) or QUAPI_ENDPOINT_INTERIOR           */
     void* cuda_stream;      /* cudaStream_t all work is issued on; NULL = the legacy default stream */
     int tune;               /* 0: default launch shape; 1: pick it by timing candidates (cached)   */
-    void* workspace;        /* optional caller-owned device buffer for the tensors, or NULL        */
+    void* workspace;        /* optional caller-owned device buffer for the tensors (16-byte
+                               aligned), or NULL                                                  */
     size_t workspace_bytes; /* its size; must be >= quapi_query_memory()'s tensor_bytes            */
     int hermitian;          /* 1: keep only (about) half of A (M = 2; needs a Hermitian rho0).
                                Swapping s+ and s- at every path point conjugates a path's weight, so
@@ -165,9 +166,10 @@ quapi_status quapi_setup_eta(const double* s, int M, const double* H, const doub
 quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* steps, int nsteps,
                              double* rho_out);
 
-/* As quapi_propagate with rho0 and rho_out in device memory (complex double),
- * enqueued on the context's stream without a host synchronisation.  steps is
- * a host array.  Errors as quapi_propagate. */
+/* As quapi_propagate with rho0 and rho_out in device memory (complex double,
+ * 16-byte aligned), enqueued on the context's stream without a host
+ * synchronisation.  steps is a host array.  Errors as quapi_propagate, and
+ * QUAPI_ERR_ARG for a device pointer that is not 16-byte aligned. */
 quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const int64_t* steps,
                                     int nsteps, void* rho_out_dev);
 
@@ -197,7 +199,10 @@ quapi_status quapi_propagate_resume(quapi_ctx* c, const int64_t* steps, int nste
  *   rho_dev    if not NULL, M*M complex double receiving rho(t_n) read out of
  *              A_{n-1} with the context's end-point treatment
  * Asynchronous on the context's stream.  A_in and A_out must not overlap.
- * Errors: QUAPI_ERR_ARG (n < 1, both outputs NULL), QUAPI_ERR_CUDA. */
+ * Every device pointer must be 16-byte aligned (cudaMalloc and PyTorch
+ * allocations are; the kernels use 16-byte vector accesses and bulk copies).
+ * Errors: QUAPI_ERR_ARG (n < 1, both outputs NULL, a misaligned pointer),
+ * QUAPI_ERR_CUDA. */
 quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, void* A_out_dev,
                                void* rho_dev);
 
@@ -242,8 +247,8 @@ quapi_status quapi_get_propagator(const quapi_ctx* c, double* U_out, double* K_o
  * make that first call before any stream capture.  All calls share the one
  * array: calls whose kernels can overlap on the GPU (different streams, or
  * several host threads) race on it and must be serialised by the caller.
- * Errors: QUAPI_ERR_ARG (NULL pointers, n < 1, M*M above the 9 partial sums a
- * slot holds), QUAPI_ERR_CUDA. */
+ * Errors: QUAPI_ERR_ARG (NULL pointers, n < 1, a pointer not 16-byte aligned,
+ * M*M above the 9 partial sums a slot holds), QUAPI_ERR_CUDA. */
 quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, const void* A_in_dev, void* rho_dev);
 
 /* Number of kernels this library has launched in this process so far (all

@@ -235,6 +235,10 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
 
 quapi_status tune_step(quapi_ctx* c);
 
+// Caller device buffers: the kernels read and write them with 16-byte vector accesses and bulk
+// copies (NULL passes; it is checked separately).
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 // Device buffers a function needs only while it runs: freed when it returns, on every path.
 struct DeviceScratch {
     std::vector<void*> ptrs;
@@ -282,6 +286,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     const size_t tensor_bytes = 2 * (size_t)nelem * elem_bytes(o.precision);
     if (o.workspace && o.workspace_bytes < tensor_bytes)
         return fail(nullptr, QUAPI_ERR_OOM, "caller workspace smaller than the two tensors");
+    if (!aligned16(o.workspace)) return fail(nullptr, QUAPI_ERR_ARG, "caller workspace must be 16-byte aligned");
 
     quapi_ctx* c = new quapi_ctx();
     c->M = M;
@@ -791,6 +796,8 @@ quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const in
                                     void* rho_out_dev) {
     if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
     if (!rho0_dev || !rho_out_dev) return fail(c, QUAPI_ERR_ARG, "rho0 and rho_out must not be NULL");
+    if (!aligned16(rho0_dev) || !aligned16(rho_out_dev))
+        return fail(c, QUAPI_ERR_ARG, "device buffers must be 16-byte aligned");
     quapi_status s = check_steps(c, steps, nsteps);
     if (s != QUAPI_OK) return s;
     return propagate_enqueue(c, static_cast<const double2*>(rho0_dev), steps, nsteps,
@@ -873,6 +880,8 @@ quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, vo
     if (!c) return fail(nullptr, QUAPI_ERR_ARG, "NULL context");
     if (n < 1) return fail(c, QUAPI_ERR_ARG, "n must be >= 1");
     if (!A_in_dev || (!A_out_dev && !rho_dev)) return fail(c, QUAPI_ERR_ARG, "need A_in and an output");
+    if (!aligned16(A_in_dev) || !aligned16(A_out_dev) || !aligned16(rho_dev))
+        return fail(c, QUAPI_ERR_ARG, "device buffers must be 16-byte aligned");
     return run_point(c, n, A_in_dev, A_out_dev, static_cast<double2*>(rho_dev));
 }
 

@@ -50,6 +50,8 @@ extern "C" quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, cons
     if (!c) return record_error(nullptr, QUAPI_ERR_ARG, "NULL context");
     if (n < 1) return record_error(c, QUAPI_ERR_ARG, "n must be >= 1");
     if (!A_in_dev || !rho_dev) return record_error(c, QUAPI_ERR_ARG, "A_in and rho must not be NULL");
+    if ((reinterpret_cast<uintptr_t>(A_in_dev) & 15u) || (reinterpret_cast<uintptr_t>(rho_dev) & 15u))
+        return record_error(c, QUAPI_ERR_ARG, "device buffers must be 16-byte aligned");
     StepArgs a;
     int M = 0, form = 0;
     cudaStream_t st = nullptr;

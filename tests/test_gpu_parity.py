@@ -340,6 +340,23 @@ def test_argument_errors(q):
         assert e.value.status == q.QUAPI_ERR_ARG
     finally:
         q.quapi_destroy(ctx)
+    # device buffers must be 16-byte aligned: rejected before any kernel runs
+    ctx = _ctx(q, pr, 3, 32)
+    try:
+        A = torch.zeros(4 ** 3 + 2, dtype=torch.complex64, device="cuda")
+        B = torch.zeros(4 ** 3 + 2, dtype=torch.complex64, device="cuda")
+        rho = torch.zeros(4, dtype=torch.complex128, device="cuda")
+        for a_in, a_out in ((A[1:], B[:-2]), (A[:-2], B[1:])):   # one complex64 = 8 bytes off
+            with pytest.raises(q.QuapiError) as e:
+                q.quapi_step_device(ctx, 4, a_in, a_out, None)
+            assert e.value.status == q.QUAPI_ERR_ARG
+        with pytest.raises(q.QuapiError) as e:
+            q.quapi_readout_static(ctx, 4, A[1:], rho)
+        assert e.value.status == q.QUAPI_ERR_ARG
+        q.quapi_step_device(ctx, 4, A[:-2], B[:-2], rho)        # aligned views work
+        torch.cuda.synchronize()
+    finally:
+        q.quapi_destroy(ctx)
 
 
 # ---------------------------------------------------------------- checkpoint / resume
