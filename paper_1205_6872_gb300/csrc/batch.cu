@@ -144,6 +144,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     cudaError_t e;
     const int M2 = M * M;
     const size_t elt = form == QUAPI_FP32 ? 8 : 16;  // complex float; complex double or double-float pair
+    if (fpt == 8 && !(M == 2 && form == QUAPI_FP32)) fpt = 4;  // 8 fibers per thread: M = 2 FP32 only
     P.M = M;
     P.form = form;
     P.fpt = fpt;
@@ -407,14 +408,15 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
     };
     if (tune && !tune_cache_lookup(sig, fpt, group)) {
         // time every candidate launch shape once (after a warm-up run) and keep the fastest
-        const int fpts[3] = {1, 2, 4};
-        const int groups[3] = {1, 4, 16};
+        const int fpts[4] = {1, 2, 4, 8};  // 8: M = 2 FP32 only (other batches run it as 4)
+        const int groups[4] = {1, 4, 8, 16};
         float best = 1e30f;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         for (int f : fpts)
             for (int g : groups) {
+                if (f == 8 && !(M0 == 2 && form0 == QUAPI_FP32)) continue;
                 Plan* P = nullptr;
                 if (get_plan(f, g, &P) != cudaSuccess) continue;
                 for (size_t j = 0; j < active.size(); ++j)

@@ -634,6 +634,9 @@ template <int M, int FORM> cudaError_t launch_batch_fpt(BatchLaunch& P, cudaStre
     switch (P.fpt) {
         case 1: return launch_batch<M, FORM, 1>(P, st, prep);
         case 4: return launch_batch<M, FORM, 4>(P, st, prep);
+        case 8:  // the plan only asks for 8 with M = 2 FP32 (its tiles are sized for the same FPT)
+            if constexpr (M == 2 && FORM == QUAPI_FP32) return launch_batch<M, FORM, 8>(P, st, prep);
+            return cudaErrorInvalidValue;
         default: return launch_batch<M, FORM, 2>(P, st, prep);
     }
 }
