@@ -13,7 +13,9 @@ host rho + quapi_destroy).  forms: the full layout, the plain FP64 form (the
 baseline the other forms' speedups refer to) and the DF64 form.  roofline:
 the dominant kernel (the fused steady-state step) timed alone with CUDA
 events on its stream; algorithmic bytes = one read and one write of every
-stored entry.
+stored entry; traffic = the ncu DRAM bytes per launch recorded in profiles/.
+t_terms_per_s = value x M^2 (each output entry sums M^2 terms).  Also in forms:
+rho at every step (allPoints) and the 256-instance batched workload.
 
 --impl reference: the FP64 CPU oracle on the host cores, a bounded sample of
 the same workload per step (a few steady-state steps on a full-size tensor).
@@ -66,6 +68,9 @@ def kernel_source_sha():
     for name in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1205_6872_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
+
+
+DATASHEET_HBM_GBPS = 7900.0  # GB300 HBM3e nominal
 
 
 def recorded_traffic(kernel_key):
@@ -575,7 +580,10 @@ def main():
                     l2="inputs larger than L2: each step streams two 1.07 GB tensors"),
         roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                       traffic=traffic, peak_source=peak_kind, kernel="herm_step_kernel<FP32> (half layout)",
-                      kernel_ms=r32h["kernel_ms"], algorithmic_bytes_per_launch=r32h["bytes"]),
+                      kernel_ms=r32h["kernel_ms"], algorithmic_bytes_per_launch=r32h["bytes"],
+                      traffic_GBps=(traffic / (r32h["kernel_ms"] / 1e3) / 1e9) if traffic else None,
+                      frac_of_datasheet=achieved / DATASHEET_HBM_GBPS),
+        t_terms_per_s=value * p.M * p.M,
         e2e=dict(value=world * ups / e2e_s, unit=UNIT, seconds_per_step=e2e_s,
                  h2d_bytes_per_step=8 * p.M + 16 * p.M * p.M * 2, d2h_bytes_per_step=16 * p.M * p.M),
         gpu_launches=int(r32h["launches"]),
