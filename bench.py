@@ -559,6 +559,15 @@ def main():
         headline_vs_fp64 = float(np.abs(r32h["rho"] - r64f["rho"]).max())
     else:
         headline_vs_fp64 = None
+    # the three-level workload (M = 3, memory length 8, 300 steps; full layout, one propagation timed)
+    if not args.no_fp64:
+        p3 = wl.three_level_L8()
+        for prec, name in ((q.QUAPI_FP32, "three_level_L8_fp32"), (q.QUAPI_FP64, "three_level_L8_fp64")):
+            r3 = time_form(q, torch, p3, prec, 1, 1, stream, world, half=False)
+            forms[name] = dict(value=world * element_updates(p3) / (r3["ms"] / 1000.0), unit=UNIT,
+                               ms_per_step=r3["ms"], layout="full", M=3, dkmax=p3.L, N=p3.N,
+                               kernel_ms=r3["kernel_ms"], kernel_GBps=r3["kernel_GBps"],
+                               kernel_frac_of_hbm=r3["kernel_GBps"] / peak)
     rap = time_all_points(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, half=True)
     forms["fp32_half_all_points"] = dict(
         value=world * ups / (rap["ms"] / 1000.0), unit=UNIT, ms_per_step=rap["ms"], layout="half",
