@@ -54,6 +54,12 @@ template <> struct FormT<QUAPI_DF64> {
     static constexpr bool kFoldLo = false;
 };
 
+// Fibers per thread of the direct kernels: the form's count for M = 2; one for M = 3, whose
+// 9-entry fibers would otherwise hold 2 x 9 inputs and outputs in registers (123 registers, 2 CTAs).
+template <int M2, int FORM> __host__ __device__ constexpr int fibers_per_thread() {
+    return M2 > 4 ? 1 : FormT<FORM>::FPT;
+}
+
 template <int M> __device__ __forceinline__ constexpr bool is_diag(int x) { return (x / M) == (x % M); }
 
 template <int M> struct Split {
@@ -94,11 +100,12 @@ __device__ __forceinline__ void st_stream(df2* p, df2 v) {
 // Loads the FPT fibers of this thread (valid[u] says whether fiber u exists).
 template <int M2, int FORM>
 __device__ __forceinline__ void load_fibers(const typename FormT<FORM>::Elem* __restrict__ A, int64_t f0,
-                                            int64_t F, typename FormT<FORM>::Elem (&a)[FormT<FORM>::FPT][M2],
-                                            bool (&valid)[FormT<FORM>::FPT]) {
-    constexpr int FPT = FormT<FORM>::FPT;
+                                            int64_t F,
+                                            typename FormT<FORM>::Elem (&a)[fibers_per_thread<M2, FORM>()][M2],
+                                            bool (&valid)[fibers_per_thread<M2, FORM>()]) {
+    constexpr int FPT = fibers_per_thread<M2, FORM>();
     using Elem = typename FormT<FORM>::Elem;
-    if constexpr (FORM == QUAPI_FP32) {
+    if constexpr (FORM == QUAPI_FP32 && FPT == 2) {
         if (f0 + 1 < F) {
             // 2 fibers = M2 * 16 bytes, 16-byte aligned because f0 is even
             const float4* p = reinterpret_cast<const float4*>(A + f0 * M2);
@@ -127,9 +134,9 @@ __device__ __forceinline__ void load_fibers(const typename FormT<FORM>::Elem* __
 
 template <int M, int FORM>
 __device__ __forceinline__ void store_row(typename FormT<FORM>::Elem* __restrict__ out, int64_t idx,
-                                          const typename FormT<FORM>::Elem (&v)[FormT<FORM>::FPT],
-                                          const bool (&valid)[FormT<FORM>::FPT]) {
-    constexpr int FPT = FormT<FORM>::FPT;
+                                          const typename FormT<FORM>::Elem (&v)[fibers_per_thread<M * M, FORM>()],
+                                          const bool (&valid)[fibers_per_thread<M * M, FORM>()]) {
+    constexpr int FPT = fibers_per_thread<M * M, FORM>();
     if constexpr (FORM == QUAPI_FP32 && M == 2) {
         if (valid[1]) {  // idx even (F even whenever 2 fibers exist)
             __stcs(reinterpret_cast<float4*>(out + idx), make_float4(v[0].x, v[0].y, v[1].x, v[1].y));
@@ -283,15 +290,16 @@ template <int M, int FORM> struct StepTables {
 // (row x at hpre[x * HSTRIDE]; all FPT fibers share one f_hi), or null to load them here.
 template <int M, int FORM, bool WRITE, bool READ, bool DIAG, int HSTRIDE = 1>
 __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
-                                               typename FormT<FORM>::Elem (&a)[FormT<FORM>::FPT][M * M],
-                                               const bool (&valid)[FormT<FORM>::FPT], int64_t f0, int64_t F,
+                                               typename FormT<FORM>::Elem (&a)[fibers_per_thread<M * M, FORM>()][M * M],
+                                               const bool (&valid)[fibers_per_thread<M * M, FORM>()], int64_t f0,
+                                               int64_t F,
                                                typename FormT<FORM>::Elem* __restrict__ out,
                                                RhoAcc<FORM> (&racc)[M * M],
                                                const typename FormT<FORM>::Tab* hpre = nullptr,
                                                const typename FormT<FORM>::Tab* hepre = nullptr) {
     constexpr int M2 = M * M;
     using Elem = typename FormT<FORM>::Elem;
-    constexpr int FPT = FormT<FORM>::FPT;
+    constexpr int FPT = fibers_per_thread<M * M, FORM>();
     uint32_t fhi[FPT], flo[FPT];
 #pragma unroll
     for (int u = 0; u < FPT; ++u) Split<M>::split((uint32_t)(f0 + u), T.lo_size, T.lo_shift, fhi[u], flo[u]);
@@ -386,7 +394,7 @@ template <int M, int FORM, bool WRITE, bool READ, bool DIAG>
 __global__ void __launch_bounds__(kThreads) step_kernel(StepArgs args) {
     constexpr int M2 = M * M;
     using Elem = typename FormT<FORM>::Elem;
-    constexpr int FPT = FormT<FORM>::FPT;
+    constexpr int FPT = fibers_per_thread<M2, FORM>();
     constexpr int TILE = kThreads * FPT;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -887,7 +895,7 @@ __global__ void rho_reduce_kernel(const double2* __restrict__ partial, int npart
 
 template <int M, int FORM, bool W, bool R, bool D>
 cudaError_t launch_variant(StepArgs& a, cudaStream_t st) {
-    constexpr int FPT = FormT<FORM>::FPT;
+    constexpr int FPT = fibers_per_thread<M * M, FORM>();
     size_t smem = StepTables<M, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = step_kernel<M, FORM, W, R, D>;
     if (smem > 48 * 1024) {
