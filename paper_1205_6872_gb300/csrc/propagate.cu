@@ -14,10 +14,12 @@
 // product with the end-point tables, summed over f instead of stored; each CTA
 // writes its partial sums (FP64) and rho_reduce_kernel adds them in CTA order.
 //
-// Memory access: every thread owns FPT consecutive fibers (FP32: 2, so that its
-// 2 outputs per row form one 16-byte store); a warp reads one contiguous span
-// of A_in and writes M2 contiguous 512-byte runs of A_out.  Persistent grid
-// (a multiple of the SM count), static tile order, streaming cache hints.
+// Memory access: every thread owns FPT consecutive fibers (FP32 with M = 2: 2, so
+// that its 2 outputs per row form one 16-byte store; otherwise 1); a warp reads one
+// contiguous span of A_in and writes M2 contiguous runs of A_out.  Persistent grid
+// (a multiple of the SM count), static tile order, streaming cache hints.  The
+// M = 2 full layout normally takes the TMA-staged kernel; the Hermitian half
+// layout has its own kernels (warp chunks of canonical positions, below).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
