@@ -733,7 +733,9 @@ __device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const t
     }
 }
 
-// Work is handed out in warp chunks of kChunk consecutive canonical positions (kChunk / 32 per lane).
+// Work is handed out in warp chunks of consecutive canonical positions (chunk / 32 per lane): 256
+// positions when the tensor is large enough to give every resident warp several chunks, fewer (down
+// to 32) for smaller tensors so that every warp still gets work.
 // Nearly every chunk lies inside one digit-1 block of level >= 2 (all but the last few levels):
 // it is decoded once and its prefixes are then consecutive plain indices, f = f0 + i with fiber
 // position h = h0 + i / 4.  Other chunks decode each position on its own.
@@ -767,19 +769,20 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
     const uint32_t cnh = (np >= 1) ? half_count32(np - 1) : 0u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nwarps = gridDim.x * (kThreads / 32);
+    const uint32_t chunk = min(kChunk, max(32u, ((npre + nwarps - 1) / nwarps + 31u) & ~31u));
 #pragma unroll 1
-    for (uint32_t cb = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * kChunk; cb < npre;
-         cb += nwarps * kChunk) {
+    for (uint32_t cb = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * chunk; cb < npre;
+         cb += nwarps * chunk) {
         uint32_t fb0, hb0;
         bool sc0, shc0;
         half_decode_pair(cb, np, fb0, sc0, hb0, shc0);
         // r1 = 4^(level - 1) of the chunk's digit-1 block (the lowest bit of f's top digit outside {0, 3});
-        // the chunk stays inside it when fb0's offset in the block + kChunk <= r1 (fb0 a multiple of 4)
+        // the chunk stays inside it when fb0's offset in the block + chunk <= r1 (fb0 a multiple of 4)
         const uint32_t t = (fb0 ^ (fb0 >> 1)) & 0x55555555u;
         const uint32_t r1 = t ? (1u << (31 - __clz(t))) : 0u;
-        const bool fast = !sc0 && !shc0 && (fb0 & 3u) == 0u && (fb0 & (r1 - 1u)) + kChunk <= r1;
+        const bool fast = !sc0 && !shc0 && (fb0 & 3u) == 0u && (fb0 & (r1 - 1u)) + chunk <= r1;
 #pragma unroll 1
-        for (uint32_t i = lane; i < kChunk; i += 32) {
+        for (uint32_t i = lane; i < chunk; i += 32) {
             const uint32_t c = cb + i;
             if (c >= npre) break;
             Elem a[4];
