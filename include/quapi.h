@@ -95,7 +95,7 @@ typedef struct {
     int tune;               /* 0: default launch shape; 1: pick it by timing candidates (cached)   */
     void* workspace;        /* optional caller-owned device buffer for the tensors (16-byte
                                aligned), or NULL                                                  */
-    size_t workspace_bytes; /* its size; must be >= quapi_query_memory()'s tensor_bytes            */
+    size_t workspace_bytes; /* its size; must be >= quapi_query_memory_opts()'s tensor_bytes       */
     int hermitian;          /* 1: keep only (about) half of A (M = 2; needs a Hermitian rho0).
                                Swapping s+ and s- at every path point conjugates a path's weight, so
                                A(conj path) = conj(A(path)) (point values 0=(+,+) 1=(+,-) 2=(-,+)
@@ -105,8 +105,8 @@ typedef struct {
                                n-1].  An n-digit tensor then stores the 4-entry last-digit fiber of
                                every canonical (n-1)-digit prefix, in that order: 2*4^(n-1) + 2^n
                                entries, prefix c at entry 4c.  Tensors passed to quapi_step_device /
-                               quapi_readout_static and the checkpoint state use this layout.  Not
-                               combinable with quapi_propagate_batch. */
+                               quapi_readout_static and the checkpoint state use this layout;
+                               quapi_propagate_batch keeps it for the instance's tensors. */
 } quapi_opts;
 
 /* Fill *opts with the defaults above. */
@@ -120,6 +120,14 @@ void quapi_opts_init(quapi_opts* opts);
  * unknown precision, or a NULL output pointer. */
 quapi_status quapi_query_memory(int M, int dkmax, int precision, size_t* tensor_bytes,
                                 size_t* total_bytes);
+
+/* As quapi_query_memory, for the precision and layout in *opts (opts->precision, opts->hermitian;
+ * the other fields are ignored): with the Hermitian half layout tensor_bytes is the two copies of
+ * its 2*4^(L-1) + 2^L stored entries, the size a caller workspace needs for it.
+ * Errors: as quapi_query_memory; QUAPI_ERR_ARG for a NULL opts; QUAPI_ERR_UNSUPPORTED for the half
+ * layout with M = 3. */
+quapi_status quapi_query_memory_opts(int M, int dkmax, const quapi_opts* opts, size_t* tensor_bytes,
+                                     size_t* total_bytes);
 
 /* Set up one problem (Sec. II's inputs).
  *   s      [M]        coordinate eigenvalues (real), the basis H is given in

@@ -779,6 +779,24 @@ quapi_status quapi_query_memory(int M, int dkmax, int precision, size_t* tensor_
     return QUAPI_OK;
 }
 
+quapi_status quapi_query_memory_opts(int M, int dkmax, const quapi_opts* opts, size_t* tensor_bytes,
+                                     size_t* total_bytes) {
+    if (!opts) return fail(nullptr, QUAPI_ERR_ARG, "NULL opts");
+    size_t t = 0, tot = 0;
+    quapi_status st = quapi_query_memory(M, dkmax, opts->precision, &t, &tot);
+    if (st != QUAPI_OK) return st;
+    if (opts->hermitian) {
+        if (M != 2) return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "the Hermitian half layout needs M = 2");
+        const size_t th = 2 * (size_t)half_entries(dkmax) * elem_bytes(opts->precision);
+        tot = tot - t + th;
+        t = th;
+    }
+    if (!tensor_bytes && !total_bytes) return fail(nullptr, QUAPI_ERR_ARG, "no output pointer");
+    if (tensor_bytes) *tensor_bytes = t;
+    if (total_bytes) *total_bytes = tot;
+    return QUAPI_OK;
+}
+
 quapi_status quapi_setup(const double* s, int M, const double* H, const quapi_spectral* J, double beta, double dt,
                          int dkmax, const quapi_opts* opts, quapi_ctx** out) {
     return setup_impl(s, M, H, J, beta, nullptr, dt, dkmax, opts, out);

@@ -39,7 +39,7 @@ QUAPI_ENDPOINT_INTERIOR = 1
 JKIND = {"ohmic_exp": QUAPI_J_OHMIC_EXP, "superohmic_gauss": QUAPI_J_SUPEROHMIC_GAUSS,
          "tabulated": QUAPI_J_TABULATED}
 
-EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_setup", "quapi_setup_eta",
+EXPORTED = ("quapi_opts_init", "quapi_query_memory", "quapi_query_memory_opts", "quapi_setup", "quapi_setup_eta",
             "quapi_propagate", "quapi_propagate_device", "quapi_step_device",
             "quapi_propagate_batch", "quapi_get_eta", "quapi_get_propagator",
             "quapi_readout_static", "quapi_get_state", "quapi_set_state", "quapi_propagate_resume",
@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
             "quapi_query_memory": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_size_t),
                                                   ctypes.POINTER(ctypes.c_size_t)]),
+            "quapi_query_memory_opts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(quapi_opts),
+                                                       ctypes.POINTER(ctypes.c_size_t),
+                                                       ctypes.POINTER(ctypes.c_size_t)]),
             "quapi_setup": (ctypes.c_int, [dp, ctypes.c_int, dp, ctypes.POINTER(quapi_spectral),
                                            ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                            ctypes.POINTER(quapi_opts), ctypes.POINTER(ctxp)]),
@@ -163,6 +166,14 @@ def quapi_opts_init(precision=QUAPI_FP64, endpoint_mode=QUAPI_ENDPOINT_STRANG, c
 def quapi_query_memory(M, dkmax, precision=QUAPI_FP64):
     t, tot = ctypes.c_size_t(), ctypes.c_size_t()
     _check(load().quapi_query_memory(int(M), int(dkmax), int(precision), ctypes.byref(t), ctypes.byref(tot)))
+    return t.value, tot.value
+
+
+def quapi_query_memory_opts(M, dkmax, opts):
+    """(tensor_bytes, total_bytes) for the precision and layout of opts (quapi_opts_init(...))."""
+    t, tot = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().quapi_query_memory_opts(int(M), int(dkmax), ctypes.byref(opts), ctypes.byref(t),
+                                          ctypes.byref(tot)))
     return t.value, tot.value
 
 

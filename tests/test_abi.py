@@ -102,3 +102,20 @@ int main(void) {
     want_o = [ctypes.sizeof(O)] + [getattr(O, f).offset for f in ("precision", "endpoint_mode", "cuda_stream", "tune",
                                                                     "workspace", "workspace_bytes", "hermitian")]
     assert [int(x) for x in lines["opts"].split()] == want_o
+
+
+def test_query_memory_opts_host_only(lib_path):
+    """Exact tensor bytes per layout and precision; the half layout needs M = 2."""
+    from paper_1205_6872_gb300 import layout, quapi
+    for prec, elt in ((quapi.QUAPI_FP32, 8), (quapi.QUAPI_FP64, 16), (quapi.QUAPI_DF64, 16)):
+        full, full_tot = quapi.quapi_query_memory_opts(2, 14, quapi.quapi_opts_init(precision=prec))
+        assert (full, full_tot) == quapi.quapi_query_memory(2, 14, prec)
+        half, half_tot = quapi.quapi_query_memory_opts(2, 14, quapi.quapi_opts_init(precision=prec, hermitian=1))
+        assert half == 2 * layout.count(14) * elt
+        assert half_tot - half == full_tot - full  # the same tables and scratch
+    with pytest.raises(quapi.QuapiError) as e:
+        quapi.quapi_query_memory_opts(3, 6, quapi.quapi_opts_init(hermitian=1))
+    assert e.value.status == quapi.QUAPI_ERR_UNSUPPORTED
+    with pytest.raises(quapi.QuapiError) as e:
+        quapi.quapi_query_memory_opts(2, 0, quapi.quapi_opts_init(hermitian=1))
+    assert e.value.status == quapi.QUAPI_ERR_ARG
