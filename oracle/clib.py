@@ -3,7 +3,9 @@
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -17,13 +19,28 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile quapi_oracle.c with gcc (-O2, OpenMP) into oracle/libquapi_oracle.so."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+    """Compile quapi_oracle.c with gcc (-O2, OpenMP) into oracle/libquapi_oracle.so.
+
+    Rebuilt whenever the source, the command or the host machine type differ from the
+    key stored beside the library (libquapi_oracle.so.buildkey), never by file times."""
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    h = hashlib.sha256()
+    with open(_SRC, "rb") as fh:
+        h.update(fh.read())
+    h.update(" ".join(cmd[:6]).encode() + b"|" + platform.machine().encode())
+    key = h.hexdigest()
+    try:
+        with open(_LIB + ".buildkey") as fh:
+            stored = fh.read().strip()
+    except OSError:
+        stored = None
+    if not force and os.path.exists(_LIB) and stored == key:
+        return _LIB
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
+    with open(_LIB + ".buildkey", "w") as fh:
+        fh.write(key + "\n")
     return _LIB
 
 
