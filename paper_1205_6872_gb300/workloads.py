@@ -160,4 +160,5 @@ CONFIGS = {
     "biased_L12": biased_L12,
     "three_level_L8": three_level_L8,
     "spin_boson_L14": spin_boson_L14,
+    "quantum_dot_L11": quantum_dot,
 }

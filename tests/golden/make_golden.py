@@ -29,6 +29,7 @@ STEPS = {
     "biased_L12": list(range(0, 31)) + list(range(40, 401, 10)),
     "three_level_L8": list(range(0, 21)) + list(range(30, 301, 10)),
     "spin_boson_L14": list(range(0, 17)) + [50, 100, 200, 300, 500, 750, 1000],
+    "quantum_dot_L11": list(range(0, 21)) + list(range(50, 1001, 50)),
 }
 
 
@@ -69,9 +70,30 @@ def run_batched():
     print(f"batched_256: {wall:.1f} s")
 
 
+def run_pulse_sweep(n=64, L=11, N=200):
+    """The paper's pulse-area sweep (Sec. III model, justFinalPoint): rho(t_N) of each instance."""
+    probs = wl.pulse_area_sweep(n=n, L=L, N=N)
+    t0 = time.time()
+    res = []
+    for i, p in enumerate(probs):
+        spec = Spectral(p.jkind, p.ja, p.wc)
+        run = oracle.OracleRun(p.s, p.H, spec, p.beta, p.dt, p.L)
+        rho = run.run(p.rho0, [p.N])
+        res.append(dict(index=i, omega=float(p.H[0, 1].real * 2.0), eta=_c(oracle.pack_eta(run.eta)),
+                        rho=_c(rho[p.N])))
+    wall = time.time() - t0
+    name = f"pulse_area_sweep_{n}"
+    with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
+        json.dump(dict(workload=name, L=L, N=N, instances=res, oracle_wall_s=wall,
+                       oracle_threads=os.environ.get("OMP_NUM_THREADS", "all")), fh)
+    print(f"{name}: {wall:.1f} s")
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:]:
-        if name == "batched_256":
+        if name == "pulse_area_sweep_64":
+            run_pulse_sweep()
+        elif name == "batched_256":
             run_batched()
         else:
             run_single(name)
