@@ -250,13 +250,16 @@ quapi_status quapi_get_propagator(const quapi_ctx* c, double* U_out, double* K_o
  *   n          >= 1: the path point whose rho(t_n) is read out
  *   A_in_dev   A_{n-1}: (M^2)^min(n,L) elements in the context's precision (device)
  *   rho_dev    M*M complex double (device), receives rho(t_n)
- * Asynchronous on the context's stream.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one
+ * Asynchronous on the context's stream.  The device current at the call
+ * must be the one that was current when the context was set up (the array's
+ * address is per device).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the one
  * array: calls whose kernels can overlap on the GPU (different streams, or
  * several host threads) race on it and must be serialised by the caller.
  * Errors: QUAPI_ERR_ARG (NULL pointers, n < 1, a pointer not 16-byte aligned,
- * M*M above the 9 partial sums a slot holds), QUAPI_ERR_CUDA. */
+ * M*M above the 9 partial sums a slot holds, a current device other than the
+ * context's), QUAPI_ERR_CUDA. */
 quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, const void* A_in_dev, void* rho_dev);
 
 /* Number of kernels this library has launched in this process so far (all

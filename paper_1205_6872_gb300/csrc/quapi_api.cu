@@ -86,6 +86,7 @@ struct quapi_ctx {
     int64_t state_n = -1;        // path point of the newest tensor kept in buf[state_buf] (-1: none)
     int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
+    int device = -1;             // CUDA device current at setup (its memory holds the context's tables)
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
     OpPlan step_first, step_steady, read_steady;
@@ -297,6 +298,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     c->endpoint = o.endpoint_mode;
     c->st = reinterpret_cast<cudaStream_t>(o.cuda_stream);
     c->host_s.assign(s, s + M);
+    cudaGetDevice(&c->device);
     c->tune = o.tune != 0;
     c->herm = o.hermitian != 0;
     {
@@ -746,6 +748,7 @@ quapi_status batch_describe(const quapi_ctx* c, int64_t N, BatchInst* inst, int*
 }
 
 uint64_t ctx_uid(const quapi_ctx* c) { return c->uid; }
+int ctx_device(const quapi_ctx* c) { return c->device; }
 bool ctx_half_layout(const quapi_ctx* c) { return c->herm; }
 bool ctx_tune_requested(const quapi_ctx* c) { return c->tune; }
 

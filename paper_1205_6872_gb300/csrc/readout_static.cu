@@ -60,8 +60,16 @@ extern "C" quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, cons
     const int M2 = M * M;
     if (M2 > kSlotWidth)
         return record_error(c, QUAPI_ERR_ARG, "quapi_readout_static: M*M exceeds its 9 partial sums per CTA");
+    // the array's address is looked up for the current device, and the kernels run on the context's
+    // tables and stream: both must be the device the context was set up on
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return record_error(c, QUAPI_ERR_CUDA, cudaGetErrorString(e));
+    if (dev != ctx_device(c))
+        return record_error(c, QUAPI_ERR_ARG,
+                            "quapi_readout_static: the current CUDA device is not the one the context was set up on");
     double2* scratch = nullptr;
-    cudaError_t e = scratch_for_current_device(&scratch);
+    e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return record_error(c, QUAPI_ERR_CUDA, cudaGetErrorString(e));
     // every launched CTA writes its own M2 slots, so nothing has to be cleared
     a.partial = scratch;
