@@ -89,6 +89,49 @@ def recorded_traffic(kernel_key):
     return None
 
 
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+
+
+def golden_rho(name):
+    """rho of the FP64 oracle stored for a workload (tests/golden/<name>.json, written by
+    tests/golden/make_golden.py from the oracle alone): {step: M x M complex}, or None if absent."""
+    try:
+        with open(os.path.join(GOLDEN_DIR, f"{name}.json")) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    out = {}
+    for k, v in d["rho"].items():
+        a = np.array(v, dtype=np.float64)
+        z = a[:, 0] + 1j * a[:, 1]
+        m = int(round(len(z) ** 0.5))
+        out[int(k)] = z.reshape(m, m)
+    return out
+
+
+def golden_instances(name):
+    """Per-instance final rho of a stored batched oracle run (list of M x M complex), or None."""
+    try:
+        with open(os.path.join(GOLDEN_DIR, f"{name}.json")) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    out = []
+    for inst in d["instances"]:
+        a = np.array(inst["rho"], dtype=np.float64)
+        z = a[:, 0] + 1j * a[:, 1]
+        m = int(round(len(z) ** 0.5))
+        out.append(z.reshape(m, m))
+    return out
+
+
+def vs_oracle(rho, gold, step):
+    """max |rho - rho_oracle| over the entries of rho at one step (None without a stored value)."""
+    if gold is None or step not in gold:
+        return None
+    return float(np.abs(np.asarray(rho).reshape(gold[step].shape) - gold[step]).max())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -351,6 +394,13 @@ def time_batched(q, torch, steps, warmup, world, rank):
         for c in c64:
             q.quapi_destroy(c)
     diff = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r32[h], r64))) for h in (0, 1, 2)}
+    gold = golden_instances("batched_256")
+    if gold is not None:
+        gold = gold[a:b]
+        vs_or = {h: replicas.reduce_max(max(float(np.abs(x - y).max()) for x, y in zip(r, gold)))
+                 for h, r in list(r32.items()) + [("fp64", list(r64))]}
+    else:
+        vs_or = {h: None for h in (0, 1, 2, "fp64")}
     total = replicas.reduce_sum(ups)
     peak, _ = measured_peaks()
     gbps = {h: replicas.reduce_sum(batch_hbm_bytes(probs, h == 1)) / batched_s[h] / 1e9 for h in (0, 1)}
@@ -363,7 +413,10 @@ def time_batched(q, torch, steps, warmup, world, rank):
                 algorithmic_GBps=gbps[1], frac_of_hbm=gbps[1] / peak,
                 full_layout_algorithmic_GBps=gbps[0], full_layout_frac_of_hbm=gbps[0] / peak,
                 df64_half_value=total / batched_s[2], df64_half_ms_per_batch=1000.0 * batched_s[2],
-                df64_half_speedup_vs_sequential_fp64=seq_s / batched_s[2], df64_half_vs_fp64_max_abs=diff[2])
+                df64_half_speedup_vs_sequential_fp64=seq_s / batched_s[2], df64_half_vs_fp64_max_abs=diff[2],
+                max_abs_vs_oracle=dict(fp32_half=vs_or[1], fp32_full=vs_or[0], df64_half=vs_or[2],
+                                       sequential_fp64=vs_or["fp64"],
+                                       reference="tests/golden/batched_256.json (FP64 oracle, rho at N = 200)"))
 
 
 def cpu_oracle_sample(p, nsteps):
@@ -528,9 +581,12 @@ def main():
     ups = element_updates(p)
     peak, peak_kind = measured_peaks()
 
+    gold = golden_rho(WORKLOAD)
+
     def form_entry(r, layout_name, ref=None):
         d = dict(value=world * ups / (r["ms"] / 1000.0), unit=UNIT, ms_per_step=r["ms"], layout=layout_name,
                  kernel_ms=r["kernel_ms"], kernel_GBps=r["kernel_GBps"], kernel_frac_of_hbm=r["kernel_GBps"] / peak,
+                 max_abs_vs_oracle=vs_oracle(r["rho"], gold, p.N),
                  rho_final=[[float(z.real), float(z.imag)] for z in r["rho"].reshape(-1)])
         if ref is not None:
             d["max_abs_vs_fp64_full"] = float(np.abs(r["rho"] - ref["rho"]).max())
@@ -539,7 +595,7 @@ def main():
     # headline: FP32 form, Hermitian half layout (the fastest configuration for a Hermitian rho0)
     r32h = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, sampler, half=True)
     value = world * ups / (r32h["ms"] / 1000.0)
-    forms = {}
+    forms = {"fp32_half": form_entry(r32h, "half")}
     r32f = time_form(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, half=False)
     forms["fp32_full"] = form_entry(r32f, "full")
     if not args.no_fp64:
@@ -575,11 +631,16 @@ def main():
                     kernel_ms=r["kernel_ms"], kernel_GBps=r["kernel_GBps"], kernel_frac_of_hbm=r["kernel_GBps"] / peak)
             forms[f"{name}_fp32_speedup_over_fp64"] = r64o["ms"] / r32o["ms"]
             forms[f"{name}_fp32_vs_fp64_max_abs"] = float(np.abs(r32o["rho"] - r64o["rho"]).max())
+            go = golden_rho(name)
+            forms[f"{name}_fp64_full"]["max_abs_vs_oracle"] = vs_oracle(r64o["rho"], go, po.N)
+            forms[f"{name}_{'fp32_half' if half else 'fp32_full'}"]["max_abs_vs_oracle"] = vs_oracle(r32o["rho"], go, po.N)
     rap = time_all_points(q, torch, p, q.QUAPI_FP32, args.steps, args.warmup, stream, world, half=True)
     forms["fp32_half_all_points"] = dict(
         value=world * ups / (rap["ms"] / 1000.0), unit=UNIT, ms_per_step=rap["ms"], layout="half",
         readout=f"allPoints: rho at all {p.N + 1} steps (readout fused into every step)",
         rho_final_vs_just_final_point=float(np.abs(rap["rhos"][-1] - r32h["rho"]).max()),
+        max_abs_vs_oracle=(max(vs_oracle(rap["rhos"][k], gold, k) for k in gold) if gold else None),
+        oracle_steps_compared=(len(gold) if gold else 0),
         max_trace_deviation=float(np.abs(np.trace(rap["rhos"], axis1=1, axis2=2) - 1.0).max()))
     if not args.no_batched:
         forms["batched_256_fp32"] = time_batched(q, torch, args.steps, args.warmup, world, rank)
@@ -605,6 +666,8 @@ def main():
         gpu_launches=int(r32h["launches"]),
         clocks=r32h["clocks"],
         max_abs_vs_fp64_full=headline_vs_fp64,
+        max_abs_vs_oracle=vs_oracle(r32h["rho"], gold, p.N),
+        oracle_reference=f"tests/golden/{WORKLOAD}.json: FP64 oracle rho at N = {p.N} (written by make_golden.py)",
         forms=forms,
         paper_context=dict(
             note="the paper's own MATLAB timings on other hardware: context, not a baseline for this workload",
@@ -614,6 +677,16 @@ def main():
             derivation="4^11 entries x 989 steady steps / 21.13 s, assuming Table 1 used the profiled 989-step run"),
         rho_final=[[float(z.real), float(z.imag)] for z in r32h["rho"].reshape(-1)],
     )
+    if not args.no_fp64:
+        # the same roofline for the FP64-accuracy form (DF64, half layout): the paper's precision
+        ach = rdfh["kernel_GBps"]
+        tr = recorded_traffic("herm_step_kernel_df64_m2")
+        line["roofline_fp64_equiv"] = dict(
+            bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak, traffic=tr, peak_source=peak_kind,
+            kernel="herm_step_kernel<DF64> (half layout)", kernel_ms=rdfh["kernel_ms"],
+            algorithmic_bytes_per_launch=rdfh["bytes"], form="df64", dtype="f32x2 (double-float, FP64-equivalent)",
+            value=world * ups / (rdfh["ms"] / 1000.0), ms_per_step=rdfh["ms"],
+            max_abs_vs_oracle=vs_oracle(rdfh["rho"], gold, p.N))
     if rank == 0 and world == 1 and not args.no_cpu:
         from oracle import clib
         nst = 2
