@@ -241,6 +241,93 @@ __device__ __forceinline__ double2 apply_hi(const double2& hi, double2 S) { retu
 __device__ __forceinline__ df2 apply_hi(const tf2& hi, const df2& S) { return tfmul(hi, S); }
 __device__ __forceinline__ float2 apply_hi(const ff2& hi, const kahan32& S) { return ffmul2(hi, S.s, S.c); }
 
+// Folded row-1 table of the half-layout step (FP32 and DF64 forms, diagonal fast path).  With the
+// fast path, rows 0 and 3 of the half layout carry only K (in hi), and row 1 (also the conjugate
+// prefix's row 1) is hi[1][fh] * lo[1][fl] * sum_old isum[1][old] A[f, old].  The product
+// lo[1][fl] isum[1][old] is formed once in FP64 at set-up (the w table, stored in the form's table
+// format); the kernel stages its row 1 in shared memory with the summed index major, W1[old][fl], so
+// that lanes with consecutive fl read consecutive entries (no bank conflicts), and the row costs one
+// table product (hi) after the sum instead of two.
+// The fast path needs at least one hi digit, so the lo table always resolves 4 digits there:
+// lo_size = 256 is a compile-time stride (the launcher checks it).
+constexpr uint32_t kFoldLo = 256;
+template <int FORM> struct FoldRow {
+    static constexpr size_t kEntryBytes = 0;
+};
+template <> struct FoldRow<QUAPI_FP32> {
+    const ff2* w;  // [4][lo_size]
+    static constexpr size_t kEntryBytes = sizeof(ff2);
+    __device__ __forceinline__ ff2 at(int q, uint32_t fl) const { return w[q * kFoldLo + fl]; }
+    __device__ __forceinline__ void stage(unsigned char* smem, const void* gw) {
+        ff2* sw = reinterpret_cast<ff2*>(smem);
+        const ff2* g = reinterpret_cast<const ff2*>(gw);
+        for (uint32_t e = threadIdx.x; e < 4 * kFoldLo; e += kThreads) {
+            const uint32_t q = e / kFoldLo, fl = e % kFoldLo;
+            sw[e] = g[(kFoldLo + fl) * 4 + q];  // w[x = 1][fl][old = q]
+        }
+        w = sw;
+    }
+};
+template <> struct FoldRow<QUAPI_DF64> {
+    const float4* w12;  // [4][lo_size] {t1.re, t1.im, t2.re, t2.im}
+    const float2* w3;   // [4][lo_size] t3
+    static constexpr size_t kEntryBytes = sizeof(float4) + sizeof(float2);
+    __device__ __forceinline__ tf2 at(int q, uint32_t fl) const {
+        const float4 a = w12[q * kFoldLo + fl];
+        tf2 t;
+        t.t1 = make_float2(a.x, a.y);
+        t.t2 = make_float2(a.z, a.w);
+        t.t3 = w3[q * kFoldLo + fl];
+        t.pad = make_float2(0.f, 0.f);
+        return t;
+    }
+    __device__ __forceinline__ void stage(unsigned char* smem, const void* gw) {
+        float4* s12 = reinterpret_cast<float4*>(smem);
+        float2* s3 = reinterpret_cast<float2*>(smem + sizeof(float4) * 4 * kFoldLo);
+        const tf2* g = reinterpret_cast<const tf2*>(gw);
+        for (uint32_t e = threadIdx.x; e < 4 * kFoldLo; e += kThreads) {
+            const uint32_t q = e / kFoldLo, fl = e % kFoldLo;
+            const tf2 t = g[(kFoldLo + fl) * 4 + q];
+            s12[e] = make_float4(t.t1.x, t.t1.y, t.t2.x, t.t2.y);
+            s3[e] = t.t3;
+        }
+        w12 = s12;
+        w3 = s3;
+    }
+};
+
+// Forms whose half-layout fast path uses the folded row: DF64, which is bound by its FP32-pipe
+// arithmetic (measured at memory length 14: 0.894 ms per step against 0.988 ms with lo and isum
+// apart).  The FP32 step stays memory-bound and runs at a 32-register cap, where the fold's extra
+// live state spills (0.376 ms against 0.370 ms); FP64 reads its own folded table through L1.
+template <int FORM> __host__ __device__ constexpr bool herm_fold() { return FORM == QUAPI_DF64; }
+
+// sum_old W1[old][fl] * a[old]: FP32 Kahan-compensated, DF64 exact products added with TwoSum
+__device__ __forceinline__ kahan32 fold_sum(const FoldRow<QUAPI_FP32>& W, uint32_t fl, const float2 (&a)[4]) {
+    kahan32 acc;
+    acc.init(ffmul(W.at(0, fl), a[0]));
+#pragma unroll
+    for (int q = 1; q < 4; ++q) acc.add(ffmul(W.at(q, fl), a[q]));
+    return acc;
+}
+// DF64: left unrenormalised (it is multiplied by hi next)
+__device__ __forceinline__ df2 fold_sum(const FoldRow<QUAPI_DF64>& W, uint32_t fl, const df2 (&a)[4]) {
+    dfacc acc;
+    acc.init_prod(W.at(0, fl), a[0]);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) acc.add_prod(W.at(q, fl), a[q]);
+    return acc.raw();
+}
+// plain sum over the oldest index for the diagonal rows of the folded variant (multiplied by hi next)
+__device__ __forceinline__ kahan32 diag_sum(const float2 (&a)[4]) { return plain_sum<4>(a); }
+__device__ __forceinline__ df2 diag_sum(const df2 (&a)[4]) {
+    dfacc acc;
+    acc.init_hl(a[0].h.x, a[0].l.x, a[0].h.y, a[0].l.y);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
+    return acc.raw();
+}
+
 // Tables of one launch: summed-digit and lo tables staged in shared memory,
 // hi tables read through L1/L2 (256 consecutive fibers share one hi entry).
 template <int M, int FORM> struct StepTables {
@@ -249,9 +336,27 @@ template <int M, int FORM> struct StepTables {
     Tab *isum, *isume, *lo, *loe;
     const Tab *hi, *hie;
     const Tab *w, *we;  // lo (x) isum: [x][f_lo][old], read through L1
+    FoldRow<FORM> w1, w1e;  // half layout, folded row 1 (step, readout) in shared memory
     uint32_t lo_size;
     int lo_shift;
     int64_t hi_size;
+
+    // shared memory of the half layout's folded variant: W1 for the step and W1e for the readout
+    static __host__ __device__ size_t fold_smem_bytes(bool write, bool read) {
+        return FoldRow<FORM>::kEntryBytes * ((write ? 1 : 0) + (read ? 1 : 0)) * 4 * (size_t)kFoldLo;
+    }
+    template <bool WRITE, bool READ>
+    __device__ __forceinline__ void stage_fold(const StepArgs& args, unsigned char* smem) {
+        hi = reinterpret_cast<const Tab*>(args.hi);
+        hie = reinterpret_cast<const Tab*>(args.hi_e);
+        lo_size = (uint32_t)args.lo_size;
+        lo_shift = args.lo_shift;
+        hi_size = args.F / args.lo_size;
+        if constexpr (FoldRow<FORM>::kEntryBytes > 0) {
+            if (WRITE) w1.stage(smem, args.w);
+            if (READ) w1e.stage(smem + (WRITE ? fold_smem_bytes(true, false) : 0), args.w_e);
+        }
+    }
 
     // shared memory of one variant: isum + lo for the step, isume + loe for the readout
     static __host__ __device__ size_t smem_bytes(int64_t lo_size, bool write, bool read) {
@@ -658,6 +763,16 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
             o[3] = apply_hi(hi[3 * T.hi_size + fh], row_sum<4>(w + ((int64_t)3 * T.lo_size + fl) * 4, a));
         }
         o[1] = apply_hi(hi[T.hi_size + fh], row_sum<4>(w + ((int64_t)T.lo_size + fl) * 4, a));
+    } else if constexpr (DIAG && herm_fold<FORM>()) {
+        // folded row 1 (lo (x) isum staged in shared memory): one table product after the sum;
+        // lo_size = 256 here, and hi has hi_size = F / 256 < 2^32 entries per row
+        const uint32_t fh8 = f >> 8, hs = (uint32_t)T.hi_size;
+        if (!ONLY1) {
+            const auto S = diag_sum(a);
+            o[0] = apply_hi(hi[fh8], S);
+            o[3] = apply_hi(hi[3u * hs + fh8], S);
+        }
+        o[1] = apply_hi(hi[hs + fh8], fold_sum(END ? T.w1e : T.w1, f & (kFoldLo - 1u), a));
     } else {
         const auto* isum = END ? T.isume : T.isum;
         const auto* lo = END ? T.loe : T.lo;
@@ -756,7 +871,10 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
     using Elem = typename FormT<FORM>::Elem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepTables<2, FORM> T;
-    T.template stage<WRITE, READ>(args, smem_raw);
+    if constexpr (DIAG && herm_fold<FORM>())
+        T.template stage_fold<WRITE, READ>(args, smem_raw);
+    else
+        T.template stage<WRITE, READ>(args, smem_raw);
     __syncthreads();
     RhoAcc<FORM> racc[4];
 #pragma unroll
@@ -903,7 +1021,7 @@ cudaError_t launch_variant(StepArgs& a, cudaStream_t st) {
     constexpr int FPT = fibers_per_thread<M * M, FORM>();
     size_t smem = StepTables<M, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = step_kernel<M, FORM, W, R, D>;
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {  // the default 48 KB includes the static shared memory
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -1041,9 +1159,11 @@ cudaError_t launch_step(int M, int form, StepArgs& a, cudaStream_t st) {
 namespace {
 template <int FORM, bool W, bool R, bool D>
 cudaError_t launch_herm_variant(StepArgs& a, cudaStream_t st) {
-    size_t smem = StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+    constexpr bool fold = D && herm_fold<FORM>();
+    if (fold && a.lo_size != kFoldLo) return cudaErrorInvalidValue;  // the fast path resolves 4 lo digits
+    size_t smem = fold ? StepTables<2, FORM>::fold_smem_bytes(W, R) : StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = herm_step_kernel<FORM, W, R, D>;
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {  // above the default 48 KB once the kernel's static shared memory is added
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }

@@ -186,6 +186,35 @@ struct dfacc {
         fast_two_sum(si, ei, r.h.y, r.l.y);
         return r;
     }
+    // Starting from the first term instead of adding it to zero (IEEE arithmetic keeps the
+    // compiler from dropping a TwoSum with 0):  = (ph + pl) + i (qh + ql)
+    __device__ __forceinline__ void init_hl(float ph, float pl, float qh, float ql) {
+        sr = ph;
+        er = pl;
+        si = qh;
+        ei = ql;
+    }
+    //  = T * x
+    __device__ __forceinline__ void init_prod(const tf2& T, const df2& x) {
+        float pb, eb, pd, ed, t;
+        tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.x, x.l.x, sr, er);  // Tre * xre
+        tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.y, x.l.y, pb, eb);  // Tim * xim
+        tf_dot_part(T.t1.x, T.t2.x, T.t3.x, x.h.y, x.l.y, si, ei);  // Tre * xim
+        tf_dot_part(T.t1.y, T.t2.y, T.t3.y, x.h.x, x.l.x, pd, ed);  // Tim * xre
+        two_sum(sr, -pb, sr, t);
+        er += t - eb;
+        two_sum(si, pd, si, t);
+        ei += t + ed;
+    }
+    // The unrenormalised pair (sr + er) + i (si + ei), for a value that is only multiplied next:
+    // a product takes the pair's two parts as they are (TwoProd of the high part, the low part's
+    // products added to the error term), so renormalising first would not change its accuracy.
+    __device__ __forceinline__ df2 raw() const {
+        df2 r;
+        r.h = make_float2(sr, si);
+        r.l = make_float2(er, ei);
+        return r;
+    }
 };
 
 // x + y for double-float complex values (TwoSum on the high parts)
@@ -339,6 +368,7 @@ struct BatchInst {
 };
 
 uint64_t ctx_uid(const ::quapi_ctx* c);            // unique per context for the process lifetime
+int ctx_device(const ::quapi_ctx* c);              // CUDA device that was current at the context's setup
 bool ctx_tune_requested(const ::quapi_ctx* c);     // quapi_opts.tune was set
 bool ctx_half_layout(const ::quapi_ctx* c);        // tensors in the Hermitian half layout
 void batch_forget(uint64_t uid);                    // drop cached batch plans using that context
