@@ -214,20 +214,22 @@ template <int M2> __device__ __forceinline__ kahan32 plain_sum(const float2 (&a)
     return acc;
 }
 
+// DF64 sums over the oldest index: started from the first term and left unrenormalised, because
+// every caller multiplies them by a table entry next (the product takes the pair as it is)
 template <int M2>
 __device__ __forceinline__ df2 row_sum(const tf2* __restrict__ isum_row, const df2 (&a)[M2]) {
     dfacc acc;
-    acc.init();
+    acc.init_prod(isum_row[0], a[0]);
 #pragma unroll
-    for (int q = 0; q < M2; ++q) acc.add_prod(isum_row[q], a[q]);
-    return acc.value();
+    for (int q = 1; q < M2; ++q) acc.add_prod(isum_row[q], a[q]);
+    return acc.raw();
 }
 template <int M2> __device__ __forceinline__ df2 plain_sum(const df2 (&a)[M2]) {
     dfacc acc;
-    acc.init();
+    acc.init_hl(a[0].h.x, a[0].l.x, a[0].h.y, a[0].l.y);
 #pragma unroll
-    for (int q = 0; q < M2; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
-    return acc.value();
+    for (int q = 1; q < M2; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
+    return acc.raw();
 }
 
 // hi * (lo * S)
@@ -301,6 +303,12 @@ template <> struct FoldRow<QUAPI_DF64> {
 // apart).  The FP32 step stays memory-bound and runs at a 32-register cap, where the fold's extra
 // live state spills (0.376 ms against 0.370 ms); FP64 reads its own folded table through L1.
 template <int FORM> __host__ __device__ constexpr bool herm_fold() { return FORM == QUAPI_DF64; }
+// The other fast path that keeps lo and isum apart (FP32): rows 0 and 3 are diagonal there and row 2
+// is written from the conjugate prefix's row 1, so only row 1 of both tables is staged (4 KB instead
+// of 16 KB per CTA, which leaves more of the SM's L1 to the hi entries).
+template <int FORM, bool DIAG> __host__ __device__ constexpr bool herm_row1() {
+    return DIAG && !herm_fold<FORM>() && !FormT<FORM>::kFoldLo;
+}
 
 // sum_old W1[old][fl] * a[old]: FP32 Kahan-compensated, DF64 exact products added with TwoSum
 __device__ __forceinline__ kahan32 fold_sum(const FoldRow<QUAPI_FP32>& W, uint32_t fl, const float2 (&a)[4]) {
@@ -318,14 +326,26 @@ __device__ __forceinline__ df2 fold_sum(const FoldRow<QUAPI_DF64>& W, uint32_t f
     for (int q = 1; q < 4; ++q) acc.add_prod(W.at(q, fl), a[q]);
     return acc.raw();
 }
-// plain sum over the oldest index for the diagonal rows of the folded variant (multiplied by hi next)
-__device__ __forceinline__ kahan32 diag_sum(const float2 (&a)[4]) { return plain_sum<4>(a); }
-__device__ __forceinline__ df2 diag_sum(const df2 (&a)[4]) {
+// Row 2 from the row-1 table: swapping s+ and s- at every point conjugates each influence factor
+// (Sec. II, Eq. for I), so lo (x) isum of row 2 at (fl, old) is the conjugate of row 1's at the
+// conjugated digits (values 1 <-> 2): sum_old conj(W1[conj old][conj fl]) a[old], flb = conj fl.
+__device__ __forceinline__ tf2 conj_tab(tf2 t) {
+    t.t1.y = -t.t1.y;
+    t.t2.y = -t.t2.y;
+    t.t3.y = -t.t3.y;
+    return t;
+}
+__device__ __forceinline__ df2 fold_sum_conj(const FoldRow<QUAPI_DF64>& W, uint32_t flb, const df2 (&a)[4]) {
     dfacc acc;
-    acc.init_hl(a[0].h.x, a[0].l.x, a[0].h.y, a[0].l.y);
-#pragma unroll
-    for (int q = 1; q < 4; ++q) acc.add_hl(a[q].h.x, a[q].l.x, a[q].h.y, a[q].l.y);
+    acc.init_prod(conj_tab(W.at(0, flb)), a[0]);
+    acc.add_prod(conj_tab(W.at(2, flb)), a[1]);
+    acc.add_prod(conj_tab(W.at(1, flb)), a[2]);
+    acc.add_prod(conj_tab(W.at(3, flb)), a[3]);
     return acc.raw();
+}
+// Full layout, M = 2, DF64 fast path: rows 1 and 2 through the folded row-1 table
+template <int M, int FORM, bool DIAG> __host__ __device__ constexpr bool full_fold() {
+    return M == 2 && DIAG && FORM == QUAPI_DF64;
 }
 
 // Tables of one launch: summed-digit and lo tables staged in shared memory,
@@ -337,6 +357,7 @@ template <int M, int FORM> struct StepTables {
     const Tab *hi, *hie;
     const Tab *w, *we;  // lo (x) isum: [x][f_lo][old], read through L1
     FoldRow<FORM> w1, w1e;  // half layout, folded row 1 (step, readout) in shared memory
+    const Tab *r1, *r1e;  // half layout fast path: row 1 of isum (4 entries) then of lo (256), shared
     uint32_t lo_size;
     int lo_shift;
     int64_t hi_size;
@@ -344,6 +365,32 @@ template <int M, int FORM> struct StepTables {
     // shared memory of the half layout's folded variant: W1 for the step and W1e for the readout
     static __host__ __device__ size_t fold_smem_bytes(bool write, bool read) {
         return FoldRow<FORM>::kEntryBytes * ((write ? 1 : 0) + (read ? 1 : 0)) * 4 * (size_t)kFoldLo;
+    }
+    // shared memory of the half layout's unfolded fast path: row 1 of isum and lo (step, readout);
+    // rows 0 and 3 are diagonal there (K only) and row 2 is written from row 1 of the conjugate prefix
+    static __host__ __device__ size_t row1_smem_bytes(int64_t lo_size, bool write, bool read) {
+        return sizeof(Tab) * ((write ? 1 : 0) + (read ? 1 : 0)) * (M2 + (size_t)lo_size);
+    }
+    template <bool WRITE, bool READ>
+    __device__ __forceinline__ void stage_row1(const StepArgs& args, unsigned char* smem) {
+        hi = reinterpret_cast<const Tab*>(args.hi);
+        hie = reinterpret_cast<const Tab*>(args.hi_e);
+        lo_size = (uint32_t)args.lo_size;
+        lo_shift = args.lo_shift;
+        hi_size = args.F / args.lo_size;
+        Tab* base = reinterpret_cast<Tab*>(smem);
+        Tab* bw = base;
+        Tab* br = base + (WRITE ? M2 + lo_size : 0);
+        const Tab* gi = reinterpret_cast<const Tab*>(args.isum);
+        const Tab* gl = reinterpret_cast<const Tab*>(args.lo);
+        const Tab* gie = reinterpret_cast<const Tab*>(args.isum_e);
+        const Tab* gle = reinterpret_cast<const Tab*>(args.lo_e);
+        for (uint32_t e = threadIdx.x; e < M2 + lo_size; e += kThreads) {
+            if (WRITE) bw[e] = e < (uint32_t)M2 ? gi[M2 + e] : gl[lo_size + (e - M2)];
+            if (READ) br[e] = e < (uint32_t)M2 ? gie[M2 + e] : gle[lo_size + (e - M2)];
+        }
+        r1 = bw;
+        r1e = br;
     }
     template <bool WRITE, bool READ>
     __device__ __forceinline__ void stage_fold(const StepArgs& args, unsigned char* smem) {
@@ -454,6 +501,20 @@ __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
                         auto Se = row_sum<M2>(T.we + ((int64_t)x * T.lo_size + flo[u]) * M2, a[u]);
                         vread[u] = apply_hi(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]], Se);
                     }
+                } else if constexpr (full_fold<M, FORM, DIAG>()) {
+                    // x = 1 or 2 (the off-diagonal rows): one table product after the folded sum
+                    if constexpr (M == 2 && FORM == QUAPI_DF64) {
+                        const uint32_t fl = flo[u] & (kFoldLo - 1u);
+                        if (WRITE) {
+                            const df2 S = (x == 1) ? fold_sum(T.w1, fl, a[u]) : fold_sum_conj(T.w1, conj_digits(fl), a[u]);
+                            vout[u] = apply_hi(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]], S);
+                        }
+                        if (READ) {
+                            const df2 Se =
+                                (x == 1) ? fold_sum(T.w1e, fl, a[u]) : fold_sum_conj(T.w1e, conj_digits(fl), a[u]);
+                            vread[u] = apply_hi(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]], Se);
+                        }
+                    }
                 } else {
                     if (WRITE) {
                         auto S = row_sum<M2>(T.isum + x * M2, a[u]);
@@ -506,7 +567,10 @@ __global__ void __launch_bounds__(kThreads) step_kernel(StepArgs args) {
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepTables<M, FORM> T;
-    T.template stage<WRITE, READ>(args, smem_raw);
+    if constexpr (full_fold<M, FORM, DIAG>())
+        T.template stage_fold<WRITE, READ>(args, smem_raw);
+    else
+        T.template stage<WRITE, READ>(args, smem_raw);
     __syncthreads();
 
     RhoAcc<FORM> racc[M2];
@@ -618,7 +682,10 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
     unsigned char* tables = reinterpret_cast<unsigned char*>(hring + HSLOTS * 2 * M2 * HPT);
 
     StepTables<M, FORM> T;
-    T.template stage<WRITE, READ>(args, tables);
+    if constexpr (full_fold<M, FORM, DIAG>())
+        T.template stage_fold<WRITE, READ>(args, tables);
+    else
+        T.template stage<WRITE, READ>(args, tables);
 
     const int64_t F = args.F;
     const int64_t ntiles = F / TILE;
@@ -768,7 +835,7 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
         // lo_size = 256 here, and hi has hi_size = F / 256 < 2^32 entries per row
         const uint32_t fh8 = f >> 8, hs = (uint32_t)T.hi_size;
         if (!ONLY1) {
-            const auto S = diag_sum(a);
+            const auto S = plain_sum<4>(a);
             o[0] = apply_hi(hi[fh8], S);
             o[3] = apply_hi(hi[3u * hs + fh8], S);
         }
@@ -776,11 +843,17 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
     } else {
         const auto* isum = END ? T.isume : T.isum;
         const auto* lo = END ? T.loe : T.lo;
+        if constexpr (herm_row1<FORM, DIAG>()) {  // row 1 of isum and lo staged on their own (stage_row1)
+            if (!ONLY1) {
+                const auto S = plain_sum<4>(a);
+                o[0] = apply_hi(hi[fh], S);
+                o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
+            }
+            const auto* r = END ? T.r1e : T.r1;  // lo_size = 256 on the fast path
+            o[1] = apply_p(hi[T.hi_size + (f >> 8)], r[4 + (f & 255u)], row_sum<4>(r, a));
+            return;
+        }
         if (ONLY1) {
-        } else if (DIAG) {
-            const auto S = plain_sum<4>(a);
-            o[0] = apply_hi(hi[fh], S);
-            o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
         } else {
             o[0] = apply_p(hi[fh], lo[fl], row_sum<4>(isum, a));
             o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4>(isum + 12, a));
@@ -873,6 +946,8 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
     StepTables<2, FORM> T;
     if constexpr (DIAG && herm_fold<FORM>())
         T.template stage_fold<WRITE, READ>(args, smem_raw);
+    else if constexpr (herm_row1<FORM, DIAG>())
+        T.template stage_row1<WRITE, READ>(args, smem_raw);
     else
         T.template stage<WRITE, READ>(args, smem_raw);
     __syncthreads();
@@ -1019,7 +1094,9 @@ __global__ void rho_reduce_kernel(const double2* __restrict__ partial, int npart
 template <int M, int FORM, bool W, bool R, bool D>
 cudaError_t launch_variant(StepArgs& a, cudaStream_t st) {
     constexpr int FPT = fibers_per_thread<M * M, FORM>();
-    size_t smem = StepTables<M, FORM>::smem_bytes(a.lo_size, W, R);
+    constexpr bool fold = full_fold<M, FORM, D>();
+    if (fold && a.lo_size != kFoldLo) return cudaErrorInvalidValue;  // the fast path resolves 4 lo digits
+    size_t smem = fold ? StepTables<M, FORM>::fold_smem_bytes(W, R) : StepTables<M, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = step_kernel<M, FORM, W, R, D>;
     if (smem > 40 * 1024) {  // the default 48 KB includes the static shared memory
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1078,7 +1155,8 @@ cudaError_t launch_tma_variant(StepArgs& a, const CUtensorMap& map, cudaStream_t
     constexpr int HPT = (kThreads * FormT<FORM>::FPT) / 256;
     size_t smem = 1024 + (size_t)STAGES * kTmaTileBytes + kBarBytes +
                   (size_t)(STAGES + 1) * 2 * 4 * HPT * sizeof(typename FormT<FORM>::Tab) +
-                  StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+                  (full_fold<2, FORM, D>() ? StepTables<2, FORM>::fold_smem_bytes(W, R)
+                                           : StepTables<2, FORM>::smem_bytes(a.lo_size, W, R));
     auto kern = step_kernel_tma<2, FORM, W, R, D, STAGES>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1161,7 +1239,9 @@ template <int FORM, bool W, bool R, bool D>
 cudaError_t launch_herm_variant(StepArgs& a, cudaStream_t st) {
     constexpr bool fold = D && herm_fold<FORM>();
     if (fold && a.lo_size != kFoldLo) return cudaErrorInvalidValue;  // the fast path resolves 4 lo digits
-    size_t smem = fold ? StepTables<2, FORM>::fold_smem_bytes(W, R) : StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
+    size_t smem = fold                      ? StepTables<2, FORM>::fold_smem_bytes(W, R)
+                  : herm_row1<FORM, D>() ? StepTables<2, FORM>::row1_smem_bytes(a.lo_size, W, R)
+                                          : StepTables<2, FORM>::smem_bytes(a.lo_size, W, R);
     auto kern = herm_step_kernel<FORM, W, R, D>;
     if (smem > 40 * 1024) {  // above the default 48 KB once the kernel's static shared memory is added
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
