@@ -461,7 +461,8 @@ def run_reference(args):
 
 
 def run_kernel_only(args):
-    """The fused steady-state step alone on the spin-boson workload at memory length --dkmax.
+    """The fused steady-state step alone on the spin-boson workload at memory length --dkmax
+    (with --with-readout: fused with the rho readout, plus the final rho reduction).
 
     One device buffer (the context's workspace) holds both tensors; 3 warm-up
     launches, then --reps timed launches.  Used for ncu captures on a small case.
@@ -485,23 +486,25 @@ def run_kernel_only(args):
     try:
         half = tbytes // 2
         A, B = ws.data_ptr(), ws.data_ptr() + half
+        rho = torch.empty(p.M * p.M, dtype=torch.complex128, device="cuda") if args.with_readout else None
         with torch.cuda.stream(stream):
             ws.view(torch.float32).normal_()
         for _ in range(3):
-            q.quapi_step_device(ctx, L + 1, A, B, None)
+            q.quapi_step_device(ctx, L + 1, A, B, rho)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for r in range(args.reps):
             src, dst = (A, B) if r % 2 == 0 else (B, A)
-            q.quapi_step_device(ctx, L + 1, src, dst, None)
+            q.quapi_step_device(ctx, L + 1, src, dst, rho)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / args.reps
     finally:
         q.quapi_destroy(ctx)
     gbs = tbytes / (ms / 1000.0) / 1e9
-    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, hermitian=bool(args.hermitian), kernel_ms=ms,
+    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, hermitian=bool(args.hermitian),
+                          with_readout=bool(args.with_readout), kernel_ms=ms,
                           GBps=gbs, logical_updates_per_s=float((p.M * p.M) ** L) / (ms / 1000.0))))
     return 0
 
@@ -553,6 +556,8 @@ def main():
                     help="form for --kernel-only / --batched-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
     ap.add_argument("--hermitian", action="store_true", help="--kernel-only / --batched-only: Hermitian half layout")
+    ap.add_argument("--with-readout", action="store_true",
+                    help="--kernel-only: the step fused with the rho readout (what allPoints runs at every step)")
     ap.add_argument("--tune", action="store_true", help="--batched-only: autotune the launch shape")
     ap.add_argument("--batched-only", action="store_true",
                     help="time only the batched launch on a seeded batch (profiling case)")

@@ -357,7 +357,7 @@ template <int M, int FORM> struct StepTables {
     const Tab *hi, *hie;
     const Tab *w, *we;  // lo (x) isum: [x][f_lo][old], read through L1
     FoldRow<FORM> w1, w1e;  // half layout, folded row 1 (step, readout) in shared memory
-    const Tab *r1, *r1e;  // half layout fast path: row 1 of isum (4 entries) then of lo (256), shared
+    const Tab* r1;  // half layout fast path: row 1 of isum (4 entries) then of lo (256), shared
     uint32_t lo_size;
     int lo_shift;
     int64_t hi_size;
@@ -366,10 +366,11 @@ template <int M, int FORM> struct StepTables {
     static __host__ __device__ size_t fold_smem_bytes(bool write, bool read) {
         return FoldRow<FORM>::kEntryBytes * ((write ? 1 : 0) + (read ? 1 : 0)) * 4 * (size_t)kFoldLo;
     }
-    // shared memory of the half layout's unfolded fast path: row 1 of isum and lo (step, readout);
-    // rows 0 and 3 are diagonal there (K only) and row 2 is written from row 1 of the conjugate prefix
+    // shared memory of the half layout's unfolded fast path: row 1 of isum and lo for the step (rows 0
+    // and 3 are diagonal there, K only, and row 2 is written from row 1 of the conjugate prefix), and the
+    // readout's folded row-1 table (loe (x) isume, formed in FP64 at set-up)
     static __host__ __device__ size_t row1_smem_bytes(int64_t lo_size, bool write, bool read) {
-        return sizeof(Tab) * ((write ? 1 : 0) + (read ? 1 : 0)) * (M2 + (size_t)lo_size);
+        return (write ? sizeof(Tab) * (M2 + (size_t)lo_size) : 0) + (read ? sizeof(Tab) * 4 * (size_t)kFoldLo : 0);
     }
     template <bool WRITE, bool READ>
     __device__ __forceinline__ void stage_row1(const StepArgs& args, unsigned char* smem) {
@@ -378,19 +379,15 @@ template <int M, int FORM> struct StepTables {
         lo_size = (uint32_t)args.lo_size;
         lo_shift = args.lo_shift;
         hi_size = args.F / args.lo_size;
-        Tab* base = reinterpret_cast<Tab*>(smem);
-        Tab* bw = base;
-        Tab* br = base + (WRITE ? M2 + lo_size : 0);
+        Tab* bw = reinterpret_cast<Tab*>(smem);
         const Tab* gi = reinterpret_cast<const Tab*>(args.isum);
         const Tab* gl = reinterpret_cast<const Tab*>(args.lo);
-        const Tab* gie = reinterpret_cast<const Tab*>(args.isum_e);
-        const Tab* gle = reinterpret_cast<const Tab*>(args.lo_e);
-        for (uint32_t e = threadIdx.x; e < M2 + lo_size; e += kThreads) {
-            if (WRITE) bw[e] = e < (uint32_t)M2 ? gi[M2 + e] : gl[lo_size + (e - M2)];
-            if (READ) br[e] = e < (uint32_t)M2 ? gie[M2 + e] : gle[lo_size + (e - M2)];
-        }
+        if (WRITE)
+            for (uint32_t e = threadIdx.x; e < M2 + lo_size; e += kThreads)
+                bw[e] = e < (uint32_t)M2 ? gi[M2 + e] : gl[lo_size + (e - M2)];
         r1 = bw;
-        r1e = br;
+        if constexpr (FoldRow<FORM>::kEntryBytes > 0)
+            if (READ) w1e.stage(smem + (WRITE ? sizeof(Tab) * (M2 + lo_size) : 0), args.w_e);
     }
     template <bool WRITE, bool READ>
     __device__ __forceinline__ void stage_fold(const StepArgs& args, unsigned char* smem) {
@@ -602,11 +599,10 @@ __global__ void __launch_bounds__(kThreads) step_kernel(StepArgs args) {
 // one 16-byte chunk of its own 64-byte slice, hit 8 different bank groups.
 // A ring of STAGES tiles per CTA (one mbarrier each) keeps STAGES x 16 KB of
 // loads in flight while the CTA computes and stores; one thread issues the
-// copies.  Every wait is bounded (globaltimer); on expiry the CTA records the
+// copies.  Every wait is bounded (globaltimer, StepArgs::wait_ns); on expiry the CTA records the
 // error flag, drains its own copies (bounded) and exits.
 constexpr int kTmaRows = 128;
 constexpr int kTmaTileBytes = kTmaRows * 128;
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 constexpr int kBarBytes = 64;                     // mbarrier slot ahead of the tables
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -622,6 +618,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_complete_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -699,7 +698,8 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
         constexpr uint32_t hb = HPT * sizeof(Tab);
         const uint32_t bytes = kTmaTileBytes + (WRITE ? M2 * hb : 0) + (READ ? M2 * hb : 0);
         const uint32_t bar = smem_u32(&bars[st]);
-        mbar_expect_tx(bar, bytes);
+        // (fault injection only: CTA 0's first tile expects more bytes than arrive, so its wait expires)
+        mbar_expect_tx(bar, bytes + ((blockIdx.x == 0 && tile == 0) ? args.fault_tx : 0u));
         tma_load_rows(smem_u32(ring + st * kTmaTileBytes), &in_map, (int32_t)(tile * kTmaRows), bar, policy);
         const int64_t fh0 = tile * HPT;
 #pragma unroll
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
         const int st = (int)(k % STAGES);
         const uint32_t parity = (uint32_t)((k / STAGES) & 1);
         const int64_t f0 = (blockIdx.x + k * gridDim.x) * TILE + (int64_t)threadIdx.x * FPT;
-        const bool ok = mbar_wait_bounded(smem_u32(&bars[st]), parity, kWaitLimitNs);
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[st]), parity, args.wait_ns);
         // this thread's FPT fibers share one f_hi (lo_size = 256 on this path): entry (threadIdx.x * FPT) / 256
         const int hsel = (int)(((int64_t)threadIdx.x * FPT) >> 8);
         const int hs = (int)(k % HSLOTS);
@@ -760,8 +760,11 @@ __global__ void __launch_bounds__(kThreads) step_kernel_tma(const __grid_constan
             // copies still in flight, and leave
             if (threadIdx.x == 0) {
                 atomicExch(args.err_flag, 1);
+                // an injected fault: account for the bytes that never come, so that the drain below
+                // waits for the tile's real copies exactly
+                if (args.fault_tx && blockIdx.x == 0 && k == 0) mbar_complete_tx(smem_u32(&bars[0]), args.fault_tx);
                 for (int64_t j = k; j < my_tiles && j < k + STAGES; ++j)
-                    mbar_wait_bounded(smem_u32(&bars[j % STAGES]), (uint32_t)((j / STAGES) & 1), kWaitLimitNs / 4);
+                    mbar_wait_bounded(smem_u32(&bars[j % STAGES]), (uint32_t)((j / STAGES) & 1), args.wait_ns / 4);
             }
             return;
         }
@@ -849,8 +852,11 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
                 o[0] = apply_hi(hi[fh], S);
                 o[3] = apply_hi(hi[3 * T.hi_size + fh], S);
             }
-            const auto* r = END ? T.r1e : T.r1;  // lo_size = 256 on the fast path
-            o[1] = apply_p(hi[T.hi_size + (f >> 8)], r[4 + (f & 255u)], row_sum<4>(r, a));
+            if constexpr (END) {  // the readout's folded row-1 table
+                o[1] = apply_hi(hi[T.hi_size + (f >> 8)], fold_sum(T.w1e, f & 255u, a));
+            } else {  // lo_size = 256 on the fast path
+                o[1] = apply_p(hi[T.hi_size + (f >> 8)], T.r1[4 + (f & 255u)], row_sum<4>(T.r1, a));
+            }
             return;
         }
         if (ONLY1) {
@@ -862,6 +868,59 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
     }
 }
 
+// Readout of the FP32 fast path, deferred per hi block.  In a fast chunk every prefix f is its own
+// conjugate's canonical partner (no self-conjugate prefixes), and a lane's fibers mostly share their hi
+// block fh = f >> 8.  Summed over the fibers of one block, the readout is
+//   rho[1] += hie[1][fh] sum W1e[.][fl] a  +  hie[1][conj fh] sum W1e[.][conj fl] b,
+//   rho[0 / 3] += 2 Re(hie[0 / 3][fh] sum_f sum_old a),
+// so the lane accumulates the three inner sums and multiplies by hie only when fh changes.  The
+// products with the hi and lo floats of W1e go to separate accumulators (the lo chain carries the
+// table's FP64 digits; the chains' roundings are random, of the order of the stored data's), and each
+// block is added to the compensated rho accumulators through one rounded product.
+template <int FORM> struct BlockRead {
+    __device__ __forceinline__ void init() {}
+};
+template <> struct BlockRead<QUAPI_FP32> {
+    float2 t1h, t1l, tbh, tbl, t0;
+    uint32_t fh;  // hi block of the sums, ~0u: none
+    __device__ __forceinline__ void init() { fh = ~0u; }
+    __device__ __forceinline__ void clear() {
+        t1h = t1l = tbh = tbl = t0 = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ static void mac(const ff2& W, float2 v, float2& h, float2& l) {
+        h.x = fmaf(W.hr, v.x, fmaf(-W.hi, v.y, h.x));
+        h.y = fmaf(W.hr, v.y, fmaf(W.hi, v.x, h.y));
+        l.x = fmaf(W.lr, v.x, fmaf(-W.li, v.y, l.x));
+        l.y = fmaf(W.lr, v.y, fmaf(W.li, v.x, l.y));
+    }
+    __device__ __forceinline__ void flush(const StepTables<2, QUAPI_FP32>& T, RhoAcc<QUAPI_FP32> (&racc)[4]) {
+        if (fh == ~0u) return;
+        const uint32_t hs = (uint32_t)T.hi_size, fhb = conj_digits(fh);
+        racc[1].add(ffmul2(T.hie[hs + fh], t1h, t1l));
+        racc[1].add(ffmul2(T.hie[hs + fhb], tbh, tbl));
+        racc[0].add_re(ffmul(T.hie[fh], t0), 2.f);
+        racc[3].add_re(ffmul(T.hie[3u * hs + fh], t0), 2.f);
+    }
+    __device__ __forceinline__ void add(const StepTables<2, QUAPI_FP32>& T, const float2 (&a)[4],
+                                        const float2 (&b)[4], uint32_t f, RhoAcc<QUAPI_FP32> (&racc)[4]) {
+        if ((f >> 8) != fh) {
+            flush(T, racc);
+            fh = f >> 8;
+            clear();
+        }
+        const uint32_t fl = f & 255u, flb = conj_digits(fl);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, fl), a[q], t1h, t1l);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, flb), b[q], tbh, tbl);
+        t0.x += (a[0].x + a[1].x) + (a[2].x + a[3].x);
+        t0.y += (a[0].y + a[1].y) + (a[2].y + a[3].y);
+    }
+};
+template <int FORM, bool DIAG> __host__ __device__ constexpr bool herm_block_read() {
+    return herm_row1<FORM, DIAG>() && FORM == QUAPI_FP32;
+}
+
 // Everything one canonical input prefix f contributes: its decoded plain digits f, whether f is its
 // own conjugate (sc), the canonical position h of fh = f >> 2 and whether fh is its own conjugate (shc).
 // The store position h (and shc) is found after the rows are computed, which keeps it out of the
@@ -870,7 +929,7 @@ template <int FORM, bool WRITE, bool READ, bool DIAG>
 __device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const typename FormT<FORM>::Elem (&a)[4],
                                            uint32_t f, bool sc, bool known, uint32_t hfast, int np, uint32_t top,
                                            uint32_t cnh, typename FormT<FORM>::Elem* __restrict__ out,
-                                           RhoAcc<FORM> (&racc)[4]) {
+                                           RhoAcc<FORM> (&racc)[4], BlockRead<FORM>& blk) {
     using Elem = typename FormT<FORM>::Elem;
     constexpr int remap[4] = {0, 2, 1, 3};
     Elem b[4];
@@ -905,6 +964,12 @@ __device__ __forceinline__ void herm_fiber(const StepTables<2, FORM>& T, const t
         }
     }
     if (READ) {
+        if constexpr (herm_block_read<FORM, DIAG>()) {
+            if (known) {  // fast chunk: deferred per hi block
+                blk.add(T, a, b, f, racc);
+                return;
+            }
+        }
         Elem r[4];
         herm_rows<FORM, DIAG, true>(T, a, f, r);
         racc[1].add(r[1]);
@@ -954,6 +1019,8 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
     RhoAcc<FORM> racc[4];
 #pragma unroll
     for (int x = 0; x < 4; ++x) racc[x].init();
+    BlockRead<FORM> blk;
+    blk.init();
     const Elem* __restrict__ A = reinterpret_cast<const Elem*>(args.A_in);
     Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
     const int np = args.half_digits;           // digits of the prefix f (n_in - 1); 32-bit indices (np <= 15)
@@ -988,9 +1055,10 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
             } else {
                 half_decode(c, np, f, sc);
             }
-            herm_fiber<FORM, WRITE, READ, DIAG>(T, a, f, sc, fast, hb0 + (i >> 2), np, top, cnh, out, racc);
+            herm_fiber<FORM, WRITE, READ, DIAG>(T, a, f, sc, fast, hb0 + (i >> 2), np, top, cnh, out, racc, blk);
         }
     }
+    if constexpr (READ && herm_block_read<FORM, DIAG>()) blk.flush(T, racc);
     if (READ) {
         // row 2 of rho is the conjugate of row 1
         __shared__ double2 red[kThreads / 32][4];

@@ -87,6 +87,8 @@ struct quapi_ctx {
     int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
     int device = -1;             // CUDA device current at setup (its memory holds the context's tables)
+    uint64_t wait_ns = 2000000000ull;  // limit of the step kernels' device-side waits
+    uint32_t fault_tx = 0;       // host-side fault injection into the TMA step (testing)
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
     OpPlan step_first, step_steady, read_steady;
@@ -341,6 +343,14 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     SCHECK(cudaMalloc(&c->d_err, sizeof(int)), "cudaMalloc(error flag)");
     SCHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st), "clear error flag");
     if (const char* v = std::getenv("QUAPI_TMA")) c->use_tma = std::atoi(v) != 0;
+    if (const char* v = std::getenv("QUAPI_WAIT_MS")) {
+        const double ms = std::atof(v);
+        if (ms > 0) c->wait_ns = (uint64_t)(ms * 1e6);
+    }
+    // host-side fault injection: CTA 0 of every TMA step expects 16 bytes more than its first tile's
+    // copies deliver, so its bounded wait expires and the call reports QUAPI_ERR_TIMEOUT
+    if (const char* f = std::getenv("QUAPI_FAULT"))
+        if (std::strcmp(f, "tma_tx") == 0) c->fault_tx = 16;
     if (const char* v = std::getenv("QUAPI_STAGES")) {
         int k = std::atoi(v);
         if (k == 2 || k == 3 || k == 4 || k == 6) c->stages = k;
@@ -497,6 +507,8 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
     a.use_tma = c->use_tma;
     a.stages = c->stages;
     a.err_flag = c->d_err;
+    a.wait_ns = c->wait_ns;
+    a.fault_tx = c->fault_tx;
     a.half_digits = c->herm ? ref->n_in - 1 : -1;
     if (c->herm)
         QCHECK(c, launch_herm_step(c->form, a, c->st), "half-layout step kernel");
@@ -703,6 +715,8 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     a->use_tma = c->use_tma;
     a->stages = c->stages;
     a->err_flag = c->d_err;
+    a->wait_ns = c->wait_ns;
+    a->fault_tx = c->fault_tx;
     a->half_digits = c->herm ? rp->n_in - 1 : -1;
     *M = c->M;
     *form = c->form;
