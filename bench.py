@@ -486,7 +486,10 @@ def run_kernel_only(args):
     try:
         half = tbytes // 2
         A, B = ws.data_ptr(), ws.data_ptr() + half
-        rho = torch.empty(p.M * p.M, dtype=torch.complex128, device="cuda") if args.with_readout else None
+        rho = (torch.empty(p.M * p.M, dtype=torch.complex128, device="cuda")
+               if (args.with_readout or args.readout_only) else None)
+        if args.readout_only:
+            B = None
         with torch.cuda.stream(stream):
             ws.view(torch.float32).normal_()
         for _ in range(3):
@@ -495,7 +498,7 @@ def run_kernel_only(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for r in range(args.reps):
-            src, dst = (A, B) if r % 2 == 0 else (B, A)
+            src, dst = (A, B) if (r % 2 == 0 or B is None) else (B, A)
             q.quapi_step_device(ctx, L + 1, src, dst, rho)
         e1.record(stream)
         e1.synchronize()
@@ -504,7 +507,7 @@ def run_kernel_only(args):
         q.quapi_destroy(ctx)
     gbs = tbytes / (ms / 1000.0) / 1e9
     print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, hermitian=bool(args.hermitian),
-                          with_readout=bool(args.with_readout), kernel_ms=ms,
+                          with_readout=bool(args.with_readout), readout_only=bool(args.readout_only), kernel_ms=ms,
                           GBps=gbs, logical_updates_per_s=float((p.M * p.M) ** L) / (ms / 1000.0))))
     return 0
 
@@ -556,6 +559,8 @@ def main():
                     help="form for --kernel-only / --batched-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")
     ap.add_argument("--hermitian", action="store_true", help="--kernel-only / --batched-only: Hermitian half layout")
+    ap.add_argument("--readout-only", action="store_true",
+                    help="--kernel-only: the rho readout alone (no tensor written; justFinalPoint's last launch)")
     ap.add_argument("--with-readout", action="store_true",
                     help="--kernel-only: the step fused with the rho readout (what allPoints runs at every step)")
     ap.add_argument("--tune", action="store_true", help="--batched-only: autotune the launch shape")
