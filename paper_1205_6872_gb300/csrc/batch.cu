@@ -2,12 +2,13 @@
 // persistent kernel launch, captured once into a CUDA graph and replayed.
 //
 // Work list.  Instances whose two tensors fit in 32 KB of shared memory
-// ("resident") are one work item each: a CTA runs all of that instance's
-// steps in shared memory.  Every other instance contributes, for each step n,
-// ceil(tiles / group) items of `group` tiles (a tile = 256 x FPT fibers or
-// growth entries).  Items are numbered resident first, then step-major
-// (wave n = step n of every instance), so an item only ever depends on items
-// with smaller numbers: a CTA takes the next number from an atomic counter,
+// ("resident") run in a kernel of their own, one CTA per instance doing all of
+// its steps in shared memory, on a side branch of the graph (concurrent with the
+// tiled kernel, which then carries neither their code nor their shared memory).
+// Every other instance contributes, for each step n, ceil(tiles / group) items
+// of `group` tiles (a tile = 256 x FPT fibers or growth entries).  Items are
+// numbered step-major (wave n = step n of every instance), so an item only ever
+// depends on items with smaller numbers: a CTA takes the next number from an atomic counter,
 // looks up its (step, instance, first tile) in a flat item table, waits
 // (bounded) until its instance has completed every tile of the previous step,
 // takes the number of its following item (the atomic's latency then overlaps
@@ -70,6 +71,9 @@ struct Plan {
     ~Plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (cap) cudaStreamDestroy(cap);
+        if (launch.side) cudaStreamDestroy(launch.side);
+        if (launch.fork) cudaEventDestroy(launch.fork);
+        if (launch.join) cudaEventDestroy(launch.join);
         if (h_rho0) cudaFreeHost(h_rho0);
         if (h_rho) cudaFreeHost(h_rho);
     }
@@ -109,6 +113,11 @@ unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin, bool he
         else units = ipow64(M2, read_nin - 1);                  // readout: fibers
     }
     return (unsigned)((units + te - 1) / te);
+}
+
+// kernels one run launches: the resident instances' kernel, the tiled instances' init and main kernels
+uint64_t kernels_per_run(const Plan& P) {
+    return (P.launch.args.nresident ? 1 : 0) + (P.launch.args.ntiled ? 2 : 0);
 }
 
 // prep = true: only set the kernel's shared-memory attribute and size the grid
@@ -155,6 +164,10 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     P.launch.fpt = fpt;
     P.launch.smem = 0;  // the largest resident instance's two tensors (none: no dynamic shared memory)
     const int te = kBThreads * fpt;
+    // the resident instances' kernel runs on a side stream, forked from and joined to the main one
+    if ((e = cudaStreamCreateWithFlags(&P.launch.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&P.launch.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&P.launch.join, cudaEventDisableTiming)) != cudaSuccess) return e;
     // per-instance buffers
     if ((e = cudaMalloc(&P.d_rho0.p, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&P.d_rho.p, sizeof(double2) * M2 * P.n)) != cudaSuccess) return e;
@@ -205,7 +218,7 @@ cudaError_t build_plan(Plan& P, const std::vector<BatchInst>& insts, int M, int 
     std::vector<uint4> items;  // tiled items in work-list order
     std::vector<unsigned> need((size_t)(nw + 1) * std::max(nt, 1), 0), ntl((size_t)(nw + 1) * std::max(nt, 1), 0);
     wave_off[0] = 0;
-    wave_off[1] = (int64_t)P.resident.size();
+    wave_off[1] = 0;  // resident instances run in their own kernel; the tiled items are numbered from 0
     std::vector<unsigned> cum(nt, 0);
     for (int n = 1; n <= nw; ++n) {
         int64_t acc = 0;
@@ -425,7 +438,7 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
                 cudaEventRecord(e0, st0);
                 if (enqueue_run(*P, st0) != cudaSuccess) continue;
                 cudaEventRecord(e1, st0);
-                count_launch(4);
+                count_launch(2 * kernels_per_run(*P));
                 if (cudaEventSynchronize(e1) != cudaSuccess) continue;
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
@@ -467,7 +480,7 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
     }
     if ((e = cudaGraphLaunch(P->exec, st0)) != cudaSuccess)
         return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
-    count_launch(P->launch.args.ntiled ? 2 : 1);
+    count_launch(kernels_per_run(*P));
     if ((e = cudaStreamSynchronize(st0)) != cudaSuccess)
         return record_error(nullptr, QUAPI_ERR_CUDA, cudaGetErrorString(e));
     int flag = 0;

@@ -39,8 +39,10 @@ struct BatchLaunch {
     int M = 0;
     int fpt = 0;
     bool half_only = false;  // every tiled instance in the half layout
-    size_t smem = 0;         // dynamic shared memory: the largest resident instance's two tensors
-    int grid = 0;            // 0: sized from the occupancy at the first launch
+    size_t smem = 0;         // dynamic shared memory of the resident kernel: the largest resident instance's tensors
+    int grid = 0;            // tiled kernel; 0: sized from the occupancy at the first launch
+    cudaStream_t side = nullptr;               // the resident kernel's stream
+    cudaEvent_t fork = nullptr, join = nullptr;  // st -> side before it, side -> st after it
 };
 
 // Per-form launchers (one translation unit each).  prep = true: only set the kernel's
@@ -405,16 +407,29 @@ __device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*
     __syncthreads();
 }
 
-// HO: every tiled instance of the batch is in the Hermitian half layout (M = 2); the full-layout tile
-// code is left out, which lowers the register need: 4 resident CTAs per SM (256 instances, FP32:
-// 82 ms per batch against 87 ms at 3 CTAs and 91 ms at 5), the general kernel 3; the DF64 form 2.
+// The shared-memory resident instances: one CTA per instance runs all of its steps (a kernel of its
+// own, on a side branch of the captured graph, so that its shared memory and registers stay out of
+// the tiled kernel).
+template <int M, int FORM>
+__global__ void __launch_bounds__(kBThreads) batch_resident_kernel(BatchArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double2 red[kBThreads / 32][M * M];
+    for (int r = blockIdx.x; r < args.nresident; r += gridDim.x) run_resident<M, FORM>(args.inst[args.resident[r]], smem, red);
+}
+
+// Minimum resident CTAs per SM of the tiled kernel (a register cap).  HO: every tiled instance of the
+// batch is in the Hermitian half layout (M = 2) and the full-layout tile code is left out.
+template <int M, int FORM, bool HO> constexpr int batch_min_ctas() {
+    if (FORM == QUAPI_DF64) return 2;
+    if (HO) return 4;
+    return M == 2 ? 3 : 1;
+}
+
 template <int M, int FORM, int FPT, bool HO>
-__global__ void __launch_bounds__(kBThreads, FORM == QUAPI_DF64 ? 2 : (HO ? 4 : ((M == 2) ? 3 : 1)))
-    batch_kernel(BatchArgs args) {
+__global__ void __launch_bounds__(kBThreads, batch_min_ctas<M, FORM, HO>()) batch_kernel(BatchArgs args) {
     constexpr int M2 = M * M;
     using Elem = typename Form<FORM>::Elem;
     constexpr int TE = kBThreads * FPT;  // fibers (or growth entries) per tile
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     __shared__ int s_stop;
     __shared__ double2 red[kBThreads / 32][M2];
@@ -429,15 +444,7 @@ __global__ void __launch_bounds__(kBThreads, FORM == QUAPI_DF64 ? 2 : (HO ? 4 : 
         const long long g = s_item;
         __syncthreads();  // every thread holds g before thread 0 writes the next number
         if (g < 0 || g >= args.total_items) break;
-        if (g < args.wave_off[1]) {
-            if (threadIdx.x == 0) {
-                const int e = *reinterpret_cast<volatile int*>(args.err);
-                s_item = e ? -1LL : (long long)atomicAdd(args.next_item, 1ull);
-            }
-            run_resident<M, FORM>(args.inst[args.resident[g]], smem, red);  // ends with a barrier
-            continue;
-        }
-        const uint4 d = args.items[g - args.wave_off[1]];
+        const uint4 d = args.items[g];
         const int n = (int)d.x, k = (int)d.y;
         const unsigned nt = args.ntiles[(int64_t)n * args.ntiled + k];
         const unsigned t0 = d.z;
@@ -611,23 +618,38 @@ __global__ void batch_init_kernel(const BatchInst* inst, const int* tiled, int n
     }
 }
 
+// Resident instances on the side stream (forked from and joined back to st through the events), the
+// tiled instances on st.
 template <int M, int FORM, int FPT> cudaError_t launch_batch(BatchLaunch& P, cudaStream_t st, bool prepare_only) {
     auto kern = P.half_only ? batch_kernel<M, FORM, FPT, (M == 2)> : batch_kernel<M, FORM, FPT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-    if (e != cudaSuccess) return e;
+    auto rkern = batch_resident_kernel<M, FORM>;
+    cudaError_t e;
+    if (P.smem > 0 && (e = cudaFuncSetAttribute(rkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem)) !=
+                          cudaSuccess)
+        return e;
     if (P.grid == 0) {
         int occ = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBThreads, P.smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBThreads, 0);
         if (e != cudaSuccess) return e;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         P.grid = std::max(1, sms * std::max(occ, 1));
     }
     if (prepare_only) return cudaSuccess;
-    if (!P.args.ntiled && !P.args.nresident) return cudaSuccess;
-    if (P.args.ntiled) batch_init_kernel<M, FORM><<<P.args.ntiled, 32, 0, st>>>(P.args.inst, P.args.tiled, P.args.ntiled);
-    kern<<<P.grid, kBThreads, P.smem, st>>>(P.args);
-    return cudaGetLastError();
+    if (P.args.nresident) {
+        if ((e = cudaEventRecord(P.fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(P.side, P.fork, 0)) != cudaSuccess) return e;
+        rkern<<<P.args.nresident, kBThreads, P.smem, P.side>>>(P.args);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(P.join, P.side)) != cudaSuccess) return e;
+    }
+    if (P.args.ntiled) {
+        batch_init_kernel<M, FORM><<<P.args.ntiled, 32, 0, st>>>(P.args.inst, P.args.tiled, P.args.ntiled);
+        kern<<<P.grid, kBThreads, 0, st>>>(P.args);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (P.args.nresident && (e = cudaStreamWaitEvent(st, P.join, 0)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 template <int M, int FORM> cudaError_t launch_batch_fpt(BatchLaunch& P, cudaStream_t st, bool prep) {
