@@ -461,7 +461,7 @@ def run_reference(args):
 
 
 def run_kernel_only(args):
-    """The fused steady-state step alone on the spin-boson workload at memory length --dkmax
+    """The fused steady-state step alone on a workload (--workload) at memory length --dkmax
     (with --with-readout: fused with the rho readout, plus the final rho reduction).
 
     One device buffer (the context's workspace) holds both tensors; 3 warm-up
@@ -471,13 +471,13 @@ def run_kernel_only(args):
     from paper_1205_6872_gb300 import quapi as q
     from paper_1205_6872_gb300 import workloads as wl
     torch.cuda.set_device(0)
-    p = wl.spin_boson_L14()
-    L = args.dkmax
+    p = wl.CONFIGS[args.workload]()
+    L = args.dkmax if args.dkmax else p.L
     prec = {"fp32": q.QUAPI_FP32, "fp64": q.QUAPI_FP64, "df64": q.QUAPI_DF64}[args.form]
     tbytes, _ = q.quapi_query_memory(p.M, L, prec)
     if args.hermitian:
         from paper_1205_6872_gb300 import layout
-        tbytes = 2 * layout.count(L) * (8 if prec == q.QUAPI_FP32 else 16)
+        tbytes = 2 * layout.count(L, p.M) * (8 if prec == q.QUAPI_FP32 else 16)
     ws = torch.empty(tbytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
     ctx = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, L,
@@ -506,7 +506,8 @@ def run_kernel_only(args):
     finally:
         q.quapi_destroy(ctx)
     gbs = tbytes / (ms / 1000.0) / 1e9
-    print(json.dumps(dict(mode="kernel-only", form=args.form, dkmax=L, hermitian=bool(args.hermitian),
+    print(json.dumps(dict(mode="kernel-only", workload=args.workload, M=p.M, form=args.form, dkmax=L,
+                          hermitian=bool(args.hermitian),
                           with_readout=bool(args.with_readout), readout_only=bool(args.readout_only), kernel_ms=ms,
                           GBps=gbs, logical_updates_per_s=float((p.M * p.M) ** L) / (ms / 1000.0))))
     return 0
@@ -554,7 +555,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-instance batched measurement")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time only the fused steady-state step kernel (profiling case)")
-    ap.add_argument("--dkmax", type=int, default=14, help="memory length for --kernel-only")
+    ap.add_argument("--dkmax", type=int, default=0, help="memory length for --kernel-only (0: the workload's)")
+    ap.add_argument("--workload", default=WORKLOAD, help="workload of --kernel-only (spin_boson_L14, three_level_L8, ...)")
     ap.add_argument("--form", default="fp32", choices=["fp32", "fp64", "df64"],
                     help="form for --kernel-only / --batched-only")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --kernel-only")

@@ -96,17 +96,23 @@ typedef struct {
     void* workspace;        /* optional caller-owned device buffer for the tensors (16-byte
                                aligned), or NULL                                                  */
     size_t workspace_bytes; /* its size; must be >= quapi_query_memory_opts()'s tensor_bytes       */
-    int hermitian;          /* 1: keep only (about) half of A (M = 2; needs a Hermitian rho0).
+    int hermitian;          /* 1: keep only (about) half of A (M = 2 or 3; needs a Hermitian rho0).
                                Swapping s+ and s- at every path point conjugates a path's weight, so
-                               A(conj path) = conj(A(path)) (point values 0=(+,+) 1=(+,-) 2=(-,+)
-                               3=(-,-); conjugation swaps 1 and 2).  A prefix is canonical when its
-                               first digit outside {0,3} is a 1; canonical prefixes of n digits are
-                               ordered [top 1: 4^(n-1) plain][top 0: canonical n-1][top 3: canonical
-                               n-1].  An n-digit tensor then stores the 4-entry last-digit fiber of
-                               every canonical (n-1)-digit prefix, in that order: 2*4^(n-1) + 2^n
-                               entries, prefix c at entry 4c.  Tensors passed to quapi_step_device /
-                               quapi_readout_static and the checkpoint state use this layout;
-                               quapi_propagate_batch keeps it for the instance's tensors. */
+                               A(conj path) = conj(A(path)): point x = (a, b) = a*M + b goes to
+                               (b, a).  Points with a = b are self-conjugate; of each other pair the
+                               point with a < b is canonical (M = 2: 0=(+,+) 1=(+,-) 2=(-,+) 3=(-,-),
+                               canonical 1, self-conjugate 0 and 3; M = 3: canonical 1, 2, 5 with
+                               conjugates 3, 6, 7, self-conjugate 0, 4, 8).  A prefix is canonical
+                               when its first digit that is not self-conjugate is canonical;
+                               canonical prefixes of n digits are ordered [each canonical top point in
+                               increasing order: (M^2)^(n-1) plain continuations][each self-
+                               conjugate top point in increasing order: canonical n-1].  An n-digit
+                               tensor stores the M^2-entry last-digit fiber of every canonical
+                               (n-1)-digit prefix, in that order: M^2 ((M^2)^(n-1) + M^(n-1))/2
+                               entries (M = 2: 2*4^(n-1) + 2^n), prefix c at entry M^2 c.  Tensors
+                               passed to quapi_step_device / quapi_readout_static and the checkpoint
+                               state use this layout; quapi_propagate_batch keeps it for the
+                               instance's tensors (M = 2). */
 } quapi_opts;
 
 /* Fill *opts with the defaults above. */
@@ -123,9 +129,8 @@ quapi_status quapi_query_memory(int M, int dkmax, int precision, size_t* tensor_
 
 /* As quapi_query_memory, for the precision and layout in *opts (opts->precision, opts->hermitian;
  * the other fields are ignored): with the Hermitian half layout tensor_bytes is the two copies of
- * its 2*4^(L-1) + 2^L stored entries, the size a caller workspace needs for it.
- * Errors: as quapi_query_memory; QUAPI_ERR_ARG for a NULL opts; QUAPI_ERR_UNSUPPORTED for the half
- * layout with M = 3. */
+ * its M^2 ((M^2)^(L-1) + M^(L-1))/2 stored entries, the size a caller workspace needs for it.
+ * Errors: as quapi_query_memory; QUAPI_ERR_ARG for a NULL opts. */
 quapi_status quapi_query_memory_opts(int M, int dkmax, const quapi_opts* opts, size_t* tensor_bytes,
                                      size_t* total_bytes);
 
@@ -225,7 +230,8 @@ quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, vo
  *   rho_final[i]   [M*M] complex (host, caller-owned): rho(t_{N_i})
  * Work runs on ctxs[0]'s stream.  Blocks until all results are written.
  * Errors: QUAPI_ERR_ARG (NULL arrays, a context twice, N_i < 0, non-Hermitian
- * rho0 for a half-layout context), QUAPI_ERR_UNSUPPORTED (mixed precision or M),
+ * rho0 for a half-layout context), QUAPI_ERR_UNSUPPORTED (mixed precision or M, or
+ * a half-layout context with M = 3),
  * QUAPI_ERR_TIMEOUT (a device-side dependency wait gave up), QUAPI_ERR_CUDA. */
 quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
                                    const int64_t* nsteps_each, double* const* rho_final);

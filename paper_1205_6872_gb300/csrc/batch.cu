@@ -364,6 +364,9 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
+        if (ctx_half_layout(ctxs[i]) && M == 3)
+            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED,
+                                "batch: the Hermitian half layout of M = 3 runs through quapi_propagate only");
         if (ctx_half_layout(ctxs[i])) {  // the half layout stores one of each conjugate pair: rho0 = rho0^dagger
             const double* r0 = rho0s[i];
             for (int r = 0; r < M; ++r)

@@ -1084,6 +1084,226 @@ __global__ void __launch_bounds__(kThreads, herm_min_ctas<FORM, WRITE, READ>()) 
     }
 }
 
+// ---- Hermitian half layout, M = 3 ---------------------------------------------------------------
+//
+// Points x = 3a + b; conjugation (a, b) -> (b, a) swaps 1 <-> 3, 2 <-> 6, 5 <-> 7 and keeps 0, 4, 8
+// (layout and index helpers in half_layout.cuh).  One thread per canonical input prefix f (np digits)
+// computes all nine rows of its fiber and stores what the layout keeps:
+//   rows 1, 2, 5 (canonical tops, blocks t = 0, 1, 2 of 9^np plain entries): out[t 9^np + f];
+//   rows 3, 6, 7: rows 1, 2, 5 of the conjugate prefix, conjugated, at out[t 9^np + conj f]
+//     (f not its own conjugate);
+//   rows 0, 4, 8 (self-conjugate tops, t' = 0, 1, 2): the fiber of the prefix (x, f / 9) at
+//     9 (9^np / 3 + t' C3(np - 1) + h) + f % 9, h = canonical position of f / 9; when f / 9 is its
+//     own conjugate that fiber keeps every last digit, and entry conj(f % 9) is the conjugate value.
+// The readout adds r_x + conj(r_conj x) for x = 1, 2, 5 (r_x alone when f is its own conjugate) and
+// 2 Re r_x (Re r_x) for x = 0, 4, 8; rows 3, 6, 7 of rho are the conjugates of rows 1, 2, 5.
+
+template <int FORM>
+__device__ __forceinline__ void load_fiber9(const typename FormT<FORM>::Elem* __restrict__ A, uint32_t c,
+                                            typename FormT<FORM>::Elem (&a)[9]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a[q] = ld_stream(A + 9ull * c + q);
+}
+
+// row x of fiber a at prefix f = (fh, fl) (step tables, or the readout's with END); Sd: the plain sum
+template <int FORM, bool DIAG, bool END, class SumT>
+__device__ __forceinline__ typename FormT<FORM>::Elem row9(const StepTables<3, FORM>& T,
+                                                           const typename FormT<FORM>::Elem (&a)[9], int x,
+                                                           uint32_t fh, uint32_t fl, const SumT& Sd) {
+    const auto* hi = END ? T.hie : T.hi;
+    const auto h = hi[(int64_t)x * T.hi_size + fh];
+    if (DIAG && is_diag<3>(x)) return apply_hi(h, Sd);
+    if constexpr (FormT<FORM>::kFoldLo) {
+        const auto* w = END ? T.we : T.w;  // lo (x) isum
+        return apply_hi(h, row_sum<9>(w + ((int64_t)x * T.lo_size + fl) * 9, a));
+    } else {
+        const auto* isum = END ? T.isume : T.isum;
+        const auto* lo = END ? T.loe : T.lo;
+        return apply_p(h, lo[x * T.lo_size + fl], row_sum<9>(isum + x * 9, a));
+    }
+}
+
+// Rows are formed one at a time and stored (or added to the readout) at once, so that only the
+// fiber and one row are live.
+template <int FORM, bool WRITE, bool READ, bool DIAG>
+__device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const typename FormT<FORM>::Elem (&a)[9],
+                                            uint32_t f, bool sc, uint32_t h, bool shc, int np, uint32_t P1,
+                                            uint32_t sbase, uint32_t cnh, typename FormT<FORM>::Elem* __restrict__ out,
+                                            RhoAcc<FORM> (&racc)[9]) {
+    using Elem = typename FormT<FORM>::Elem;
+    uint32_t fh, fl;
+    Split<3>::split(f, T.lo_size, T.lo_shift, fh, fl);
+    decltype(plain_sum<9>(a)) Sd;
+    if (DIAG) Sd = plain_sum<9>(a);
+    if (WRITE) {
+        const uint32_t f0 = f % 9u;
+        const uint32_t e0 = 9u * (sbase + h) + f0;  // rows 0, 4, 8: their fibers are C3(np - 1) prefixes apart
+        const uint32_t e1 = e0 - f0 + conj3(f0);
+        const uint32_t fb = sc ? f : conj_digits3(f, np);
+#pragma unroll
+        for (int x = 0; x < 9; ++x) {
+            const Elem v = row9<FORM, DIAG, false>(T, a, x, fh, fl, Sd);
+            if (np == 0) {  // one-digit output: every point stored
+                st_stream(out + x, v);
+                continue;
+            }
+            if (x == 1 || x == 2 || x == 5) {
+                st_stream(out + (x == 1 ? 0u : (x == 2 ? P1 : 2u * P1)) + f, v);
+            } else if (x == 3 || x == 6 || x == 7) {  // rows 1, 2, 5 of the conjugate prefix
+                if (!sc) st_stream(out + (x == 3 ? 0u : (x == 6 ? P1 : 2u * P1)) + fb, conjv(v));
+            } else {
+                const uint32_t off = (x == 0 ? 0u : (x == 4 ? 9u * cnh : 18u * cnh));
+                st_stream(out + e0 + off, v);
+                if (!sc && shc) st_stream(out + e1 + off, conjv(v));  // self-conjugate (x, f / 9): every last digit
+            }
+        }
+    }
+    if (READ) {
+#pragma unroll
+        for (int x = 0; x < 9; ++x) {
+            const Elem r = row9<FORM, DIAG, true>(T, a, x, fh, fl, Sd);
+            if (x == 1 || x == 2 || x == 5) {
+                racc[x].add(r);
+            } else if (x == 3 || x == 6 || x == 7) {
+                if (!sc) racc[conj3(x)].add(conjv(r));
+            } else {
+                racc[x].add_re(r, sc ? 1 : 2);
+            }
+        }
+    }
+}
+
+// Minimum resident CTAs per SM given to the compiler (nine-entry fibers: many live values)
+template <int FORM, bool WRITE, bool READ> constexpr int herm3_min_ctas() {
+    return (FORM == QUAPI_FP32 && WRITE && !READ) ? 3 : 2;
+}
+
+template <int FORM, bool WRITE, bool READ, bool DIAG>
+__global__ void __launch_bounds__(kThreads, herm3_min_ctas<FORM, WRITE, READ>()) herm3_step_kernel(StepArgs args) {
+    using Elem = typename FormT<FORM>::Elem;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepTables<3, FORM> T;
+    T.template stage<WRITE, READ>(args, smem_raw);
+    __syncthreads();
+    RhoAcc<FORM> racc[9];
+#pragma unroll
+    for (int x = 0; x < 9; ++x) racc[x].init();
+    const Elem* __restrict__ A = reinterpret_cast<const Elem*>(args.A_in);
+    Elem* __restrict__ out = reinterpret_cast<Elem*>(args.A_out);
+    const int np = args.half_digits;  // digits of the prefix f (n_in - 1); base-9 indices in 32 bits
+    const uint32_t npre = half3_count(np);
+    const uint32_t P1 = pow9(np);                          // plain block of a canonical top in the output
+    const uint32_t sbase = (np >= 1) ? P1 / 3u : 0u;       // 3 x 9^(np-1): first self-conjugate output prefix
+    const uint32_t cnh = (np >= 1) ? half3_count(np - 1) : 0u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nwarps = gridDim.x * (kThreads / 32);
+    const uint32_t chunk = min(kChunk, max(32u, ((npre + nwarps - 1) / nwarps + 31u) & ~31u));
+#pragma unroll 1
+    for (uint32_t cb = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * chunk; cb < npre;
+         cb += nwarps * chunk) {
+        // a chunk inside one plain block of a canonical top digit (level >= 2) is decoded once: its
+        // prefixes are consecutive plain indices, and so are the positions of their f / 9
+        uint32_t fb0, hb0, run;
+        bool sc0, shc0;
+        half3_decode_run(cb, np, fb0, sc0, hb0, shc0, run);
+        const bool fast = run >= min(chunk, npre - cb);
+        const uint32_t r0 = fb0 % 9u;
+#pragma unroll 1
+        for (uint32_t i = lane; i < chunk; i += 32) {
+            const uint32_t c = cb + i;
+            if (c >= npre) break;
+            Elem a[9];
+            load_fiber9<FORM>(A, c, a);
+            uint32_t f, h;
+            bool sc, shc;
+            if (fast) {
+                f = fb0 + i;
+                h = hb0 + (r0 + i) / 9u;
+                sc = false;
+                shc = false;
+            } else {
+                half3_decode_pair(c, np, f, sc, h, shc);
+            }
+            herm3_fiber<FORM, WRITE, READ, DIAG>(T, a, f, sc, h, shc, np, P1, sbase, cnh, out, racc);
+        }
+    }
+    if (READ) {
+        // rows 3, 6, 7 of rho are the conjugates of rows 1, 2, 5
+        __shared__ double2 red[kThreads / 32][9];
+        const int wl = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int x = 0; x < 9; ++x) {
+            if (x == 3 || x == 6 || x == 7) continue;
+            double2 v = racc[x].value();
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+                v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+            }
+            if (wl == 0) red[warp][x] = v;
+        }
+        __syncthreads();
+        const int x = threadIdx.x;
+        if (x < 9 && x != 3 && x != 6 && x != 7) {
+            double2 v = make_double2(0.0, 0.0);
+            for (int w = 0; w < kThreads / 32; ++w) v = cadd(v, red[w][x]);
+            args.partial[(int64_t)blockIdx.x * 9 + x] = v;
+            if (x == 1 || x == 2 || x == 5) args.partial[(int64_t)blockIdx.x * 9 + conj3(x)] = make_double2(v.x, -v.y);
+        }
+    }
+}
+
+// growth in the M = 3 half layout: input n_in digits -> n_in + 1 digits, one thread per stored entry
+// e = 9 c + d of canonical (or self-conjugate) input prefix c.  With i = (P, d) the plain input index:
+// rows 1, 2, 5 at i in their plain blocks (unless P is its own conjugate and d is 3, 6 or 7: that entry
+// is the conjugate write of (P, conj d)); rows 3, 6, 7 as rows 1, 2, 5 at conj i with conj A (unless P
+// is its own conjugate and d is not 1, 2 or 5: i is self-conjugate, or the write is (P, conj d)'s);
+// rows 0, 4, 8 at the fiber of the prefix (x, P), entry d.
+template <int FORM>
+__global__ void __launch_bounds__(kThreads) herm3_grow_kernel(const void* __restrict__ A_in_, void* __restrict__ A_out_,
+                                                              int n_in, const void* __restrict__ lo_,
+                                                              const void* __restrict__ hi_, int64_t lo_size_) {
+    using Elem = typename FormT<FORM>::Elem;
+    using Tab = typename FormT<FORM>::Tab;
+    const Elem* A = reinterpret_cast<const Elem*>(A_in_);
+    Elem* out = reinterpret_cast<Elem*>(A_out_);
+    const Tab* lo = reinterpret_cast<const Tab*>(lo_);
+    const Tab* hi = reinterpret_cast<const Tab*>(hi_);
+    const uint32_t S = pow9(n_in);              // plain block of a canonical top in the output
+    const uint32_t Cp = half3_count(n_in - 1);  // canonical prefixes of the input
+    const uint32_t sbase = S / 3u;              // 3 x 9^(n_in - 1)
+    const uint32_t lo_size = (uint32_t)lo_size_;
+    const int64_t hi_size = S / lo_size;
+    const int64_t entries = 9 * (int64_t)Cp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < entries; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = (uint32_t)(e / 9), d = (uint32_t)(e % 9);
+        uint32_t P;
+        bool scP;
+        half3_decode(c, n_in - 1, P, scP);
+        const uint32_t i = P * 9u + d;
+        const Elem v = A[e];
+        auto Pm = [&](int x, uint32_t idx, Elem w) {
+            return tmul(hi[(int64_t)x * hi_size + idx / lo_size], tmul(lo[(int64_t)x * lo_size + idx % lo_size], w));
+        };
+        const bool dtop = (d == 1u || d == 2u || d == 5u);
+        if (!(scP && !dtop && !self3(d))) {
+            out[i] = Pm(1, i, v);
+            out[S + i] = Pm(2, i, v);
+            out[2u * S + i] = Pm(5, i, v);
+        }
+        if (!scP || dtop) {
+            const uint32_t ib = conj_digits3(i, n_in);
+            const Elem vb = conjv(v);
+            out[ib] = Pm(1, ib, vb);
+            out[S + ib] = Pm(2, ib, vb);
+            out[2u * S + ib] = Pm(5, ib, vb);
+        }
+        out[9u * (sbase + c) + d] = Pm(0, i, v);
+        out[9u * (sbase + Cp + c) + d] = Pm(4, i, v);
+        out[9u * (sbase + 2u * Cp + c) + d] = Pm(8, i, v);
+    }
+}
+
 // growth in the half layout: input n_in digits -> n_in + 1 digits, one thread per stored entry
 template <int FORM>
 __global__ void __launch_bounds__(kThreads) herm_grow_kernel(const void* __restrict__ A_in_, void* __restrict__ A_out_,
@@ -1363,6 +1583,69 @@ cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, 
         herm_grow_kernel<QUAPI_FP32><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size, lo_shift);
     else if (form == QUAPI_DF64)
         herm_grow_kernel<QUAPI_DF64><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size, lo_shift);
+    else
+        return cudaErrorInvalidValue;
+    count_launch();
+    return cudaGetLastError();
+}
+
+namespace {
+template <int FORM, bool W, bool R, bool D>
+cudaError_t launch_herm3_variant(StepArgs& a, cudaStream_t st) {
+    const size_t smem = StepTables<3, FORM>::smem_bytes(a.lo_size, W, R);
+    auto kern = herm3_step_kernel<FORM, W, R, D>;
+    if (smem > 40 * 1024) {  // the default 48 KB includes the static shared memory
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t work = ((int64_t)half3_count(a.half_digits) + kThreads - 1) / kThreads;
+    int64_t g = (int64_t)num_sms() * (occ < 1 ? 1 : occ);
+    if (g > work) g = work;
+    if (g > a.grid) g = a.grid;
+    if (g < 1) g = 1;
+    a.grid = (int)g;
+    kern<<<a.grid, kThreads, smem, st>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+template <int FORM>
+cudaError_t launch_herm3_form(StepArgs& a, cudaStream_t st) {
+    const bool W = a.A_out != nullptr, R = a.partial != nullptr;
+    if (a.diag_fast) {
+        if (W && R) return launch_herm3_variant<FORM, true, true, true>(a, st);
+        if (W) return launch_herm3_variant<FORM, true, false, true>(a, st);
+        if (R) return launch_herm3_variant<FORM, false, true, true>(a, st);
+    } else {
+        if (W && R) return launch_herm3_variant<FORM, true, true, false>(a, st);
+        if (W) return launch_herm3_variant<FORM, true, false, false>(a, st);
+        if (R) return launch_herm3_variant<FORM, false, true, false>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t launch_herm3_step(int form, StepArgs& a, cudaStream_t st) {
+    if (form == QUAPI_FP64) return launch_herm3_form<QUAPI_FP64>(a, st);
+    if (form == QUAPI_FP32) return launch_herm3_form<QUAPI_FP32>(a, st);
+    if (form == QUAPI_DF64) return launch_herm3_form<QUAPI_DF64>(a, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_herm3_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
+                              int64_t lo_size, cudaStream_t st) {
+    const int64_t Cn = half3_entries(n_in);
+    int64_t blocks = (Cn + kThreads - 1) / kThreads;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+    if (blocks < 1) blocks = 1;
+    if (form == QUAPI_FP64)
+        herm3_grow_kernel<QUAPI_FP64><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size);
+    else if (form == QUAPI_FP32)
+        herm3_grow_kernel<QUAPI_FP32><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size);
+    else if (form == QUAPI_DF64)
+        herm3_grow_kernel<QUAPI_DF64><<<(unsigned)blocks, kThreads, 0, st>>>(A_in, A_out, n_in, lo, hi, lo_size);
     else
         return cudaErrorInvalidValue;
     count_launch();

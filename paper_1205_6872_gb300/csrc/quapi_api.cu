@@ -56,10 +56,10 @@ int max_dkmax(int M) { return M == 2 ? 16 : 10; }
 constexpr int kMaxTableNodes = 65536;          // tabulated J: largest table
 constexpr int64_t kMaxEtaPanels = int64_t(1) << 22;  // tabulated J: largest panel count
 
-// stored entries of an n-digit tensor in the Hermitian half layout: 4 C(n-1), C(m) = (4^m + 2^m)/2
-int64_t half_entries(int n) {
+// stored entries of an n-digit tensor in the Hermitian half layout: M^2 C(n-1), C(m) = ((M^2)^m + M^m)/2
+int64_t half_entries(int M, int n) {
     if (n == 0) return 1;
-    return 4 * (((int64_t(1) << (2 * (n - 1))) + (int64_t(1) << (n - 1))) >> 1);
+    return (int64_t)M * M * ((ipow((int64_t)M * M, n - 1) + ipow(M, n - 1)) >> 1);
 }
 int lo_digits_max(int M) { return M == 2 ? 4 : 2; }
 
@@ -82,7 +82,7 @@ struct quapi_ctx {
     bool use_tma = true;         // M = 2: TMA-staged step kernel when the tensor allows it
     int stages = 2;              // its ring depth (2 measured best: 4 CTAs per SM fit)
     bool tune = false;           // quapi_opts.tune
-    bool herm = false;           // Hermitian half layout (M = 2)
+    bool herm = false;           // Hermitian half layout (M = 2 or 3)
     int64_t state_n = -1;        // path point of the newest tensor kept in buf[state_buf] (-1: none)
     int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
@@ -231,7 +231,6 @@ quapi_status check_common(const double* s, int M, const double* H, double dt, in
             return fail(nullptr, QUAPI_ERR_ARG, "precision must be QUAPI_FP64, QUAPI_FP32 or QUAPI_DF64");
         if (o->endpoint_mode != QUAPI_ENDPOINT_STRANG && o->endpoint_mode != QUAPI_ENDPOINT_INTERIOR)
             return fail(nullptr, QUAPI_ERR_ARG, "unknown endpoint_mode");
-        if (o->hermitian && M != 2) return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "the Hermitian half layout needs M = 2");
     }
     return QUAPI_OK;
 }
@@ -285,7 +284,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
         if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, QUAPI_ERR_ARG, "beta must be > 0");
     }
     const int M2 = M * M;
-    const int64_t nelem = o.hermitian ? half_entries(L) : ipow(M2, L);
+    const int64_t nelem = o.hermitian ? half_entries(M, L) : ipow(M2, L);
     const size_t tensor_bytes = 2 * (size_t)nelem * elem_bytes(o.precision);
     if (o.workspace && o.workspace_bytes < tensor_bytes)
         return fail(nullptr, QUAPI_ERR_OOM, "caller workspace smaller than the two tensors");
@@ -510,7 +509,9 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
     a.wait_ns = c->wait_ns;
     a.fault_tx = c->fault_tx;
     a.half_digits = c->herm ? ref->n_in - 1 : -1;
-    if (c->herm)
+    if (c->herm && c->M == 3)
+        QCHECK(c, launch_herm3_step(c->form, a, c->st), "half-layout step kernel");
+    else if (c->herm)
         QCHECK(c, launch_herm_step(c->form, a, c->st), "half-layout step kernel");
     else
         QCHECK(c, launch_step(c->M, c->form, a, c->st), "step kernel");
@@ -521,6 +522,12 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
 quapi_status run_grow_op(quapi_ctx* c, const OpPlan& gp, const void* A_in, void* A_out) {
     int sh = 0;
     while ((int64_t(1) << sh) < gp.lo_size) ++sh;
+    if (c->herm && c->M == 3) {
+        QCHECK(c, launch_herm3_grow(c->form, A_in, A_out, gp.n_in, c->d_tables + gp.off_lo, c->d_tables + gp.off_hi,
+                                    gp.lo_size, c->st),
+               "half-layout grow kernel");
+        return QUAPI_OK;
+    }
     if (c->herm) {
         QCHECK(c, launch_herm_grow(c->form, A_in, A_out, gp.n_in, c->d_tables + gp.off_lo, c->d_tables + gp.off_hi,
                                    gp.lo_size, sh, c->st),
@@ -676,7 +683,7 @@ quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int6
 
 int64_t state_elements(const quapi_ctx* c, int64_t n) {
     const int d = (int)std::min<int64_t>(n + 1, c->L);
-    return c->herm ? half_entries(d) : ipow(c->M2, d);
+    return c->herm ? half_entries(c->M, d) : ipow(c->M2, d);
 }
 
 quapi_status ensure_slots(quapi_ctx* c, int nsteps) {
@@ -803,8 +810,7 @@ quapi_status quapi_query_memory_opts(int M, int dkmax, const quapi_opts* opts, s
     quapi_status st = quapi_query_memory(M, dkmax, opts->precision, &t, &tot);
     if (st != QUAPI_OK) return st;
     if (opts->hermitian) {
-        if (M != 2) return fail(nullptr, QUAPI_ERR_UNSUPPORTED, "the Hermitian half layout needs M = 2");
-        const size_t th = 2 * (size_t)half_entries(dkmax) * elem_bytes(opts->precision);
+        const size_t th = 2 * (size_t)half_entries(M, dkmax) * elem_bytes(opts->precision);
         tot = tot - t + th;
         t = th;
     }

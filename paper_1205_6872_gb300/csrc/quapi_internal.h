@@ -306,7 +306,7 @@ struct StepArgs {
     bool use_tma;         // M = 2: stage input tiles with 2-D TMA copies when the tensor allows it
     int stages;           // TMA ring depth (2, 3, 4 or 6)
     int* err_flag;        // set to 1 by a CTA whose bounded wait expired
-    int half_digits;      // Hermitian half layout: digits of the fiber prefix (n_in - 1)
+    int half_digits;      // Hermitian half layout (M = 2 or 3): digits of the fiber prefix (n_in - 1)
     uint64_t wait_ns;     // limit of every device-side wait (QUAPI_WAIT_MS at set-up; default 2 s)
     uint32_t fault_tx;    // host-side fault injection (QUAPI_FAULT=tma_tx at set-up): bytes added to the
                           // first tile's expected transfer in CTA 0 of the TMA step, so that its wait expires
@@ -318,6 +318,9 @@ cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t 
 cudaError_t launch_herm_step(int form, StepArgs& a, cudaStream_t st);  // sets a.grid
 cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
                              int64_t lo_size, int lo_shift, cudaStream_t st);
+cudaError_t launch_herm3_step(int form, StepArgs& a, cudaStream_t st);  // M = 3 half layout; sets a.grid
+cudaError_t launch_herm3_grow(int form, const void* A_in, void* A_out, int n_in, const void* lo, const void* hi,
+                              int64_t lo_size, cudaStream_t st);
 cudaError_t launch_rho_reduce(const double2* partial, int nparts, int M2, double2* rho_out,
                               cudaStream_t st);
 cudaError_t launch_init_tensor(const double2* rho0_dev, const double2* eta, int self0_idx,

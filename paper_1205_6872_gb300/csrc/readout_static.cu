@@ -74,7 +74,8 @@ extern "C" quapi_status quapi_readout_static(const quapi_ctx* c, int64_t n, cons
     // every launched CTA writes its own M2 slots, so nothing has to be cleared
     a.partial = scratch;
     a.grid = kStaticCtas;
-    e = (a.half_digits >= 0) ? launch_herm_step(form, a, st) : launch_step(M, form, a, st);
+    e = (a.half_digits >= 0) ? (M == 3 ? launch_herm3_step(form, a, st) : launch_herm_step(form, a, st))
+                             : launch_step(M, form, a, st);
     if (e != cudaSuccess) return record_error(c, QUAPI_ERR_CUDA, cudaGetErrorString(e));
     e = launch_rho_reduce(scratch, a.grid, M2, static_cast<double2*>(rho_dev), st);
     if (e != cudaSuccess) return record_error(c, QUAPI_ERR_CUDA, cudaGetErrorString(e));

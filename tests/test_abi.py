@@ -105,17 +105,15 @@ int main(void) {
 
 
 def test_query_memory_opts_host_only(lib_path):
-    """Exact tensor bytes per layout and precision; the half layout needs M = 2."""
+    """Exact tensor bytes per layout and precision, for M = 2 and M = 3."""
     from paper_1205_6872_gb300 import layout, quapi
-    for prec, elt in ((quapi.QUAPI_FP32, 8), (quapi.QUAPI_FP64, 16), (quapi.QUAPI_DF64, 16)):
-        full, full_tot = quapi.quapi_query_memory_opts(2, 14, quapi.quapi_opts_init(precision=prec))
-        assert (full, full_tot) == quapi.quapi_query_memory(2, 14, prec)
-        half, half_tot = quapi.quapi_query_memory_opts(2, 14, quapi.quapi_opts_init(precision=prec, hermitian=1))
-        assert half == 2 * layout.count(14) * elt
-        assert half_tot - half == full_tot - full  # the same tables and scratch
-    with pytest.raises(quapi.QuapiError) as e:
-        quapi.quapi_query_memory_opts(3, 6, quapi.quapi_opts_init(hermitian=1))
-    assert e.value.status == quapi.QUAPI_ERR_UNSUPPORTED
+    for M, L in ((2, 14), (3, 8), (3, 1)):
+        for prec, elt in ((quapi.QUAPI_FP32, 8), (quapi.QUAPI_FP64, 16), (quapi.QUAPI_DF64, 16)):
+            full, full_tot = quapi.quapi_query_memory_opts(M, L, quapi.quapi_opts_init(precision=prec))
+            assert (full, full_tot) == quapi.quapi_query_memory(M, L, prec)
+            half, half_tot = quapi.quapi_query_memory_opts(M, L, quapi.quapi_opts_init(precision=prec, hermitian=1))
+            assert half == 2 * layout.count(L, M) * elt
+            assert half_tot - half == full_tot - full  # the same tables and scratch
     with pytest.raises(quapi.QuapiError) as e:
         quapi.quapi_query_memory_opts(2, 0, quapi.quapi_opts_init(hermitian=1))
     assert e.value.status == quapi.QUAPI_ERR_ARG

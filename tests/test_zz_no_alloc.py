@@ -7,7 +7,8 @@ sums in a fixed array inside the library instead.  This file is collected last
 on purpose, and each check runs the new entry point twice in a row, because
 every call reuses that one array.  It covers the three precisions (FP64, FP32,
 the double-float DF64 form) and both tensor layouts (full, and the Hermitian
-half layout of M = 2, where row 2 of rho is written as the conjugate of row 1).
+half layout, where the rows of rho below the diagonal are written as the
+conjugates of the rows above it), for M = 2 and M = 3.
 """
 
 import numpy as np
@@ -32,7 +33,7 @@ def _to_dev(a, prec):
 
 
 CASES = [(2, 6, 3, 0), (2, 6, 6, 0), (2, 6, 9, 0), (2, 12, 20, 0), (3, 4, 7, 0),
-         (2, 6, 3, 1), (2, 6, 9, 1), (2, 12, 20, 1), (2, 1, 4, 1)]
+         (2, 6, 3, 1), (2, 6, 9, 1), (2, 12, 20, 1), (2, 1, 4, 1), (3, 4, 7, 1), (3, 6, 6, 1)]
 
 
 @pytest.mark.parametrize("prec", [64, 32, 48])
@@ -48,7 +49,7 @@ def test_readout_static_matches_step_readout(M, L, n, half, prec):
                             q.quapi_opts_init(precision=prec, hermitian=half))
     try:
         d = min(n, L)
-        entries = layout.count(d) if half else (M * M) ** d
+        entries = layout.count(d, M) if half else (M * M) ** d
         A = _to_dev(wl.random_tensor(entries, seed=n + L), prec)
         want = torch.zeros(M * M, dtype=torch.complex128, device="cuda")
         q.quapi_step_device(ctx, n, A, None, want)
