@@ -1105,32 +1105,35 @@ __device__ __forceinline__ void load_fiber9(const typename FormT<FORM>::Elem* __
     for (int q = 0; q < 9; ++q) a[q] = ld_stream(A + 9ull * c + q);
 }
 
-// row x of fiber a at prefix f = (fh, fl) (step tables, or the readout's with END); Sd: the plain sum
-template <int FORM, bool DIAG, bool END, class SumT>
-__device__ __forceinline__ typename FormT<FORM>::Elem row9(const StepTables<3, FORM>& T,
-                                                           const typename FormT<FORM>::Elem (&a)[9], int x,
-                                                           uint32_t fh, uint32_t fl, const SumT& Sd) {
-    const auto* hi = END ? T.hie : T.hi;
-    const auto h = hi[(int64_t)x * T.hi_size + fh];
-    if (DIAG && is_diag<3>(x)) return apply_hi(h, Sd);
+// The sum over the oldest index of row x, multiplied by lo (FP64: the folded lo (x) isum sum): the row
+// is then hi[x][fh] times it (step tables, or the readout's with END).
+template <int FORM, bool END>
+__device__ __forceinline__ auto lo_sum9(const StepTables<3, FORM>& T, const typename FormT<FORM>::Elem (&a)[9], int x,
+                                        uint32_t fl) {
     if constexpr (FormT<FORM>::kFoldLo) {
         const auto* w = END ? T.we : T.w;  // lo (x) isum
-        return apply_hi(h, row_sum<9>(w + ((int64_t)x * T.lo_size + fl) * 9, a));
+        return row_sum<9>(w + ((int64_t)x * T.lo_size + fl) * 9, a);
+    } else if constexpr (FORM == QUAPI_FP32) {
+        const kahan32 S = row_sum<9>((END ? T.isume : T.isum) + x * 9, a);
+        return ffmul2((END ? T.loe : T.lo)[x * T.lo_size + fl], S.s, S.c);
     } else {
-        const auto* isum = END ? T.isume : T.isum;
-        const auto* lo = END ? T.loe : T.lo;
-        return apply_p(h, lo[x * T.lo_size + fl], row_sum<9>(isum + x * 9, a));
+        return tfmul((END ? T.loe : T.lo)[x * T.lo_size + fl], row_sum<9>((END ? T.isume : T.isum) + x * 9, a));
     }
 }
 
-// Rows are formed one at a time and stored (or added to the readout) at once, so that only the
-// fiber and one row are live.
-template <int FORM, bool WRITE, bool READ, bool DIAG>
+// Rows are formed one at a time and stored (or added to the readout) at once, so that only the fiber
+// and one row are live.  The influence factors of the summed and the lo digits depend on the new
+// point x only through d(x) = s_a - s_b (Sec. II, Eq. for I; K sits in hi on the fast path), so for
+// equally spaced coordinate eigenvalues (EQS: s_1 - s_0 = s_2 - s_1) rows 1 and 5 (d = s_0 - s_1) and
+// rows 3 and 7 (d = s_1 - s_0) have equal isum and lo rows and share that part of the work.
+template <int FORM, bool WRITE, bool READ, bool DIAG, bool EQS>
 __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const typename FormT<FORM>::Elem (&a)[9],
-                                            uint32_t f, bool sc, uint32_t h, bool shc, int np, uint32_t P1,
+                                            uint32_t f, uint32_t fb, bool sc, uint32_t h, bool shc, int np, uint32_t P1,
                                             uint32_t sbase, uint32_t cnh, typename FormT<FORM>::Elem* __restrict__ out,
                                             RhoAcc<FORM> (&racc)[9]) {
     using Elem = typename FormT<FORM>::Elem;
+    constexpr bool SHARE = EQS && DIAG;
+    constexpr int order[9] = {1, 5, 3, 7, 2, 6, 0, 4, 8};  // the sharing pairs next to each other
     uint32_t fh, fl;
     Split<3>::split(f, T.lo_size, T.lo_shift, fh, fl);
     decltype(plain_sum<9>(a)) Sd;
@@ -1139,10 +1142,18 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
         const uint32_t f0 = f % 9u;
         const uint32_t e0 = 9u * (sbase + h) + f0;  // rows 0, 4, 8: their fibers are C3(np - 1) prefixes apart
         const uint32_t e1 = e0 - f0 + conj3(f0);
-        const uint32_t fb = sc ? f : conj_digits3(f, np);
+        decltype(lo_sum9<FORM, false>(T, a, 0, fl)) ls;
 #pragma unroll
-        for (int x = 0; x < 9; ++x) {
-            const Elem v = row9<FORM, DIAG, false>(T, a, x, fh, fl, Sd);
+        for (int k = 0; k < 9; ++k) {
+            const int x = order[k];
+            const auto hx = T.hi[(int64_t)x * T.hi_size + fh];
+            Elem v;
+            if (DIAG && is_diag<3>(x)) {
+                v = apply_hi(hx, Sd);
+            } else {
+                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, false>(T, a, x, fl);
+                v = tmul(hx, ls);
+            }
             if (np == 0) {  // one-digit output: every point stored
                 st_stream(out + x, v);
                 continue;
@@ -1159,9 +1170,18 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
         }
     }
     if (READ) {
+        decltype(lo_sum9<FORM, true>(T, a, 0, fl)) ls;
 #pragma unroll
-        for (int x = 0; x < 9; ++x) {
-            const Elem r = row9<FORM, DIAG, true>(T, a, x, fh, fl, Sd);
+        for (int k = 0; k < 9; ++k) {
+            const int x = order[k];
+            const auto hx = T.hie[(int64_t)x * T.hi_size + fh];
+            Elem r;
+            if (DIAG && is_diag<3>(x)) {
+                r = apply_hi(hx, Sd);
+            } else {
+                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, true>(T, a, x, fl);
+                r = tmul(hx, ls);
+            }
             if (x == 1 || x == 2 || x == 5) {
                 racc[x].add(r);
             } else if (x == 3 || x == 6 || x == 7) {
@@ -1178,7 +1198,7 @@ template <int FORM, bool WRITE, bool READ> constexpr int herm3_min_ctas() {
     return (FORM == QUAPI_FP32 && WRITE && !READ) ? 3 : 2;
 }
 
-template <int FORM, bool WRITE, bool READ, bool DIAG>
+template <int FORM, bool WRITE, bool READ, bool DIAG, bool EQS>
 __global__ void __launch_bounds__(kThreads, herm3_min_ctas<FORM, WRITE, READ>()) herm3_step_kernel(StepArgs args) {
     using Elem = typename FormT<FORM>::Elem;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1198,6 +1218,7 @@ __global__ void __launch_bounds__(kThreads, herm3_min_ctas<FORM, WRITE, READ>())
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nwarps = gridDim.x * (kThreads / 32);
     const uint32_t chunk = min(kChunk, max(32u, ((npre + nwarps - 1) / nwarps + 31u) & ~31u));
+    uint32_t qc = ~0u, cq = 0;  // fast path: the conjugate of f / 81 (digits above the last two), per lane
 #pragma unroll 1
     for (uint32_t cb = (blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5)) * chunk; cb < npre;
          cb += nwarps * chunk) {
@@ -1214,17 +1235,24 @@ __global__ void __launch_bounds__(kThreads, herm3_min_ctas<FORM, WRITE, READ>())
             if (c >= npre) break;
             Elem a[9];
             load_fiber9<FORM>(A, c, a);
-            uint32_t f, h;
+            uint32_t f, h, fb;
             bool sc, shc;
-            if (fast) {
+            if (fast) {  // np >= 2 here
                 f = fb0 + i;
                 h = hb0 + (r0 + i) / 9u;
                 sc = false;
                 shc = false;
+                const uint32_t qf = f / 81u, r = f - 81u * qf;
+                if (qf != qc) {
+                    qc = qf;
+                    cq = 81u * conj_digits3(qf, np - 2);
+                }
+                fb = cq + 9u * conj3(r / 9u) + conj3(r % 9u);
             } else {
                 half3_decode_pair(c, np, f, sc, h, shc);
+                fb = sc ? f : conj_digits3(f, np);
             }
-            herm3_fiber<FORM, WRITE, READ, DIAG>(T, a, f, sc, h, shc, np, P1, sbase, cnh, out, racc);
+            herm3_fiber<FORM, WRITE, READ, DIAG, EQS>(T, a, f, fb, sc, h, shc, np, P1, sbase, cnh, out, racc);
         }
     }
     if (READ) {
@@ -1590,10 +1618,10 @@ cudaError_t launch_herm_grow(int form, const void* A_in, void* A_out, int n_in, 
 }
 
 namespace {
-template <int FORM, bool W, bool R, bool D>
+template <int FORM, bool W, bool R, bool D, bool EQS = false>
 cudaError_t launch_herm3_variant(StepArgs& a, cudaStream_t st) {
     const size_t smem = StepTables<3, FORM>::smem_bytes(a.lo_size, W, R);
-    auto kern = herm3_step_kernel<FORM, W, R, D>;
+    auto kern = herm3_step_kernel<FORM, W, R, D, EQS>;
     if (smem > 40 * 1024) {  // the default 48 KB includes the static shared memory
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1614,7 +1642,11 @@ cudaError_t launch_herm3_variant(StepArgs& a, cudaStream_t st) {
 template <int FORM>
 cudaError_t launch_herm3_form(StepArgs& a, cudaStream_t st) {
     const bool W = a.A_out != nullptr, R = a.partial != nullptr;
-    if (a.diag_fast) {
+    if (a.diag_fast && a.eq_spaced) {
+        if (W && R) return launch_herm3_variant<FORM, true, true, true, true>(a, st);
+        if (W) return launch_herm3_variant<FORM, true, false, true, true>(a, st);
+        if (R) return launch_herm3_variant<FORM, false, true, true, true>(a, st);
+    } else if (a.diag_fast) {
         if (W && R) return launch_herm3_variant<FORM, true, true, true>(a, st);
         if (W) return launch_herm3_variant<FORM, true, false, true>(a, st);
         if (R) return launch_herm3_variant<FORM, false, true, true>(a, st);

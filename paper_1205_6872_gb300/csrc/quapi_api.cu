@@ -87,6 +87,7 @@ struct quapi_ctx {
     int state_buf = 0;
     uint64_t uid = 0;            // never reused within the process
     int device = -1;             // CUDA device current at setup (its memory holds the context's tables)
+    int eq_spaced = 0;           // M = 3 with s_1 - s_0 = s_2 - s_1 (exactly, in FP64)
     uint64_t wait_ns = 2000000000ull;  // limit of the step kernels' device-side waits
     uint32_t fault_tx = 0;       // host-side fault injection into the TMA step (testing)
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
@@ -299,6 +300,8 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     c->endpoint = o.endpoint_mode;
     c->st = reinterpret_cast<cudaStream_t>(o.cuda_stream);
     c->host_s.assign(s, s + M);
+    // d(x) = s_a - s_b computed the same way as the table kernel: equal values give bitwise equal rows
+    c->eq_spaced = (M == 3 && (s[0] - s[1]) == (s[1] - s[2])) ? 1 : 0;
     cudaGetDevice(&c->device);
     c->tune = o.tune != 0;
     c->herm = o.hermitian != 0;
@@ -506,6 +509,7 @@ quapi_status run_step_op(quapi_ctx* c, const OpPlan* sp, const OpPlan* rp, const
     a.use_tma = c->use_tma;
     a.stages = c->stages;
     a.err_flag = c->d_err;
+    a.eq_spaced = c->eq_spaced;
     a.wait_ns = c->wait_ns;
     a.fault_tx = c->fault_tx;
     a.half_digits = c->herm ? ref->n_in - 1 : -1;
@@ -722,6 +726,7 @@ quapi_status readout_launch_args(const quapi_ctx* c, int64_t n, const void* A_in
     a->use_tma = c->use_tma;
     a->stages = c->stages;
     a->err_flag = c->d_err;
+    a->eq_spaced = c->eq_spaced;
     a->wait_ns = c->wait_ns;
     a->fault_tx = c->fault_tx;
     a->half_digits = c->herm ? rp->n_in - 1 : -1;

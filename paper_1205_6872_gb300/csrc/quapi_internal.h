@@ -307,6 +307,7 @@ struct StepArgs {
     int stages;           // TMA ring depth (2, 3, 4 or 6)
     int* err_flag;        // set to 1 by a CTA whose bounded wait expired
     int half_digits;      // Hermitian half layout (M = 2 or 3): digits of the fiber prefix (n_in - 1)
+    int eq_spaced;        // M = 3: equally spaced s (rows with equal s_a - s_b share isum and lo rows)
     uint64_t wait_ns;     // limit of every device-side wait (QUAPI_WAIT_MS at set-up; default 2 s)
     uint32_t fault_tx;    // host-side fault injection (QUAPI_FAULT=tma_tx at set-up): bytes added to the
                           // first tile's expected transfer in CTA 0 of the TMA step, so that its wait expires

@@ -35,10 +35,15 @@ def q():
     return quapi
 
 
+S3_UNEVEN = np.array([-1.0, 0.3, 1.0])  # unequally spaced: rows 1 and 5 (and 3 and 7) differ
+
+
 @pytest.mark.parametrize("prec", [64, 32, 48])
-@pytest.mark.parametrize("L,n", [(4, 1), (4, 2), (4, 3), (4, 4), (4, 5), (4, 11), (1, 1), (1, 3), (2, 2),
-                                 (6, 6), (6, 9), (7, 8)])
-def test_m3_half_layout_single_step(q, L, n, prec):
+@pytest.mark.parametrize("L,n,uneven", [(4, 1, 0), (4, 2, 0), (4, 3, 0), (4, 4, 0), (4, 5, 0), (4, 11, 0), (1, 1, 0),
+                                        (1, 3, 0), (2, 2, 0), (6, 6, 0), (6, 9, 0), (7, 8, 0),
+                                        (4, 3, 1), (4, 5, 1), (6, 9, 1), (7, 8, 1)])
+def test_m3_half_layout_single_step(q, L, n, uneven, prec):
+    s3 = S3_UNEVEN if uneven else S3
     H = wl.random_hermitian(3, 50 + L)
     eta = wl.random_eta(L, seed=400 + L + n)
     etad = oracle.unpack_eta(eta, L)
@@ -46,12 +51,12 @@ def test_m3_half_layout_single_step(q, L, n, prec):
     n_in = min(n, L)
     A = ly.symmetrize(wl.random_tensor(9 ** n_in, seed=n + 11 * L), n_in, 3)
     A = ly.from_half(representable(ly.to_half(A, n_in, 3), prec), n_in, 3)  # what the device stores
-    G, g, _, summed = rec.step_tables(etad, S3, K, L, n)
+    G, g, _, summed = rec.step_tables(etad, s3, K, L, n)
     want = rec.apply_step(A, G, g, n_in, summed)
     out_digits = n_in if summed else n_in + 1
-    Gr, gr, _ = rec.readout_tables(etad, S3, K, L, n)
+    Gr, gr, _ = rec.readout_tables(etad, s3, K, L, n)
     want_rho = rec.apply_readout(A, Gr, gr, n_in)
-    ctx = q.quapi_setup_eta(S3, H, eta, 0.2, L, q.quapi_opts_init(precision=prec, hermitian=1))
+    ctx = q.quapi_setup_eta(s3, H, eta, 0.2, L, q.quapi_opts_init(precision=prec, hermitian=1))
     try:
         dA = _to_dev(ly.to_half(A, n_in, 3), prec)
         dout = _empty_dev(ly.count(out_digits, 3), prec)
