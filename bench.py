@@ -209,7 +209,7 @@ def element_updates(p):
 
 def tensor_entries(p, half):
     from paper_1205_6872_gb300 import layout
-    return layout.count(p.L) if half else (p.M * p.M) ** p.L
+    return layout.count(p.L, p.M) if half else (p.M * p.M) ** p.L
 
 
 def entry_bytes(q, precision):
@@ -333,7 +333,7 @@ def batch_hbm_bytes(probs, half, entry_bytes=8, resident_bytes=32 * 1024):
         M2 = p.M * p.M
         if 2 * M2 ** p.L * entry_bytes <= resident_bytes:
             continue
-        stored = (lambda n: ly.count(n)) if half else (lambda n: M2 ** n)
+        stored = (lambda n: ly.count(n, p.M)) if half else (lambda n: M2 ** n)
         for n in range(1, p.N + 1):
             if n < p.L and n < p.N:
                 total += (stored(n) + stored(n + 1)) * entry_bytes
