@@ -26,6 +26,7 @@ from paper_1205_6872_gb300 import workloads as wl  # noqa: E402
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 STEPS = {
+    "spin_boson_L6": list(range(0, 101)),
     "biased_L12": list(range(0, 31)) + list(range(40, 401, 10)),
     "three_level_L8": list(range(0, 21)) + list(range(30, 301, 10)),
     "spin_boson_L14": list(range(0, 17)) + [50, 100, 200, 300, 500, 750, 1000],

@@ -46,7 +46,7 @@ def q():
 
 
 @pytest.mark.parametrize("prec", [64, 32, 48])
-@pytest.mark.parametrize("name", ["biased_L12", "three_level_L8", "spin_boson_L14"])
+@pytest.mark.parametrize("name", ["spin_boson_L6", "biased_L12", "three_level_L8", "spin_boson_L14"])
 def test_workload_against_stored_oracle(q, name, prec):
     p = wl.CONFIGS[name]()
     g = _golden(name)
