@@ -873,31 +873,30 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
 // block fh = f >> 8.  Summed over the fibers of one block, the readout is
 //   rho[1] += hie[1][fh] sum W1e[.][fl] a  +  hie[1][conj fh] sum W1e[.][conj fl] b,
 //   rho[0 / 3] += 2 Re(hie[0 / 3][fh] sum_f sum_old a),
-// so the lane accumulates the three inner sums and multiplies by hie only when fh changes.  The
-// products with the hi and lo floats of W1e go to separate accumulators (the lo chain carries the
-// table's FP64 digits; the chains' roundings are random, of the order of the stored data's), and each
-// block is added to the compensated rho accumulators through one rounded product.
+// so the lane accumulates the three inner sums and multiplies by hie only when fh changes.  The inner
+// sums are FP32 products (the hi float of W1e) in FMA chains of at most a block's fibers, of the order
+// of the stored data's own rounding (an accumulator for the table's lo floats changed the error against
+// the oracle by less than 1e-15 at memory length 14, and cost 6 % more time); each block is added to
+// the compensated rho accumulators through one rounded product with the double-float hie.
 template <int FORM> struct BlockRead {
     __device__ __forceinline__ void init() {}
 };
 template <> struct BlockRead<QUAPI_FP32> {
-    float2 t1h, t1l, tbh, tbl, t0;
+    float2 t1h, tbh, t0;
     uint32_t fh;  // hi block of the sums, ~0u: none
     __device__ __forceinline__ void init() { fh = ~0u; }
     __device__ __forceinline__ void clear() {
-        t1h = t1l = tbh = tbl = t0 = make_float2(0.f, 0.f);
+        t1h = tbh = t0 = make_float2(0.f, 0.f);
     }
-    __device__ __forceinline__ static void mac(const ff2& W, float2 v, float2& h, float2& l) {
+    __device__ __forceinline__ static void mac(const ff2& W, float2 v, float2& h) {
         h.x = fmaf(W.hr, v.x, fmaf(-W.hi, v.y, h.x));
         h.y = fmaf(W.hr, v.y, fmaf(W.hi, v.x, h.y));
-        l.x = fmaf(W.lr, v.x, fmaf(-W.li, v.y, l.x));
-        l.y = fmaf(W.lr, v.y, fmaf(W.li, v.x, l.y));
     }
     __device__ __forceinline__ void flush(const StepTables<2, QUAPI_FP32>& T, RhoAcc<QUAPI_FP32> (&racc)[4]) {
         if (fh == ~0u) return;
         const uint32_t hs = (uint32_t)T.hi_size, fhb = conj_digits(fh);
-        racc[1].add(ffmul2(T.hie[hs + fh], t1h, t1l));
-        racc[1].add(ffmul2(T.hie[hs + fhb], tbh, tbl));
+        racc[1].add(ffmul(T.hie[hs + fh], t1h));
+        racc[1].add(ffmul(T.hie[hs + fhb], tbh));
         racc[0].add_re(ffmul(T.hie[fh], t0), 2.f);
         racc[3].add_re(ffmul(T.hie[3u * hs + fh], t0), 2.f);
     }
@@ -910,9 +909,9 @@ template <> struct BlockRead<QUAPI_FP32> {
         }
         const uint32_t fl = f & 255u, flb = conj_digits(fl);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, fl), a[q], t1h, t1l);
+        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, fl), a[q], t1h);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, flb), b[q], tbh, tbl);
+        for (int q = 0; q < 4; ++q) mac(T.w1e.at(q, flb), b[q], tbh);
         t0.x += (a[0].x + a[1].x) + (a[2].x + a[3].x);
         t0.y += (a[0].y + a[1].y) + (a[2].y + a[3].y);
     }
@@ -996,10 +995,10 @@ constexpr uint32_t kChunk = 256;
 
 // Minimum resident CTAs per SM given to the compiler (a register cap).  Measured at memory length 14:
 // the FP32 step runs best at 8 CTAs (32 registers; 0.370 ms against 0.380 ms at 6 CTAs and
-// 0.425 ms uncapped), the FP32 step with the readout at 3 (0.687 ms against 0.725 ms at 4);
-// the readout alone, and the DF64 and FP64 forms, at 3-4.
+// 0.425 ms uncapped), the FP32 step with the per-block readout at 4 (64 registers, no spills;
+// 0.561 ms, 0.562 at 3); the readout alone, and the DF64 and FP64 forms, at 3-4.
 template <int FORM, bool WRITE, bool READ> constexpr int herm_min_ctas() {
-    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 8 : (WRITE ? 3 : 4);
+    if (FORM == QUAPI_FP32) return (WRITE && !READ) ? 8 : 4;
     if (WRITE && READ) return 3;
     return (FORM == QUAPI_DF64 && READ) ? 3 : 4;
 }
