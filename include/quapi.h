@@ -112,7 +112,7 @@ typedef struct {
                                entries (M = 2: 2*4^(n-1) + 2^n), prefix c at entry M^2 c.  Tensors
                                passed to quapi_step_device / quapi_readout_static and the checkpoint
                                state use this layout; quapi_propagate_batch keeps it for the
-                               instance's tensors (M = 2). */
+                               instance's tensors. */
 } quapi_opts;
 
 /* Fill *opts with the defaults above. */
@@ -230,8 +230,7 @@ quapi_status quapi_step_device(quapi_ctx* c, int64_t n, const void* A_in_dev, vo
  *   rho_final[i]   [M*M] complex (host, caller-owned): rho(t_{N_i})
  * Work runs on ctxs[0]'s stream.  Blocks until all results are written.
  * Errors: QUAPI_ERR_ARG (NULL arrays, a context twice, N_i < 0, non-Hermitian
- * rho0 for a half-layout context), QUAPI_ERR_UNSUPPORTED (mixed precision or M, or
- * a half-layout context with M = 3),
+ * rho0 for a half-layout context), QUAPI_ERR_UNSUPPORTED (mixed precision or M),
  * QUAPI_ERR_TIMEOUT (a device-side dependency wait gave up), QUAPI_ERR_CUDA. */
 quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, const double* const* rho0s,
                                    const int64_t* nsteps_each, double* const* rho_final);

@@ -96,17 +96,18 @@ int64_t ipow64(int64_t b, int e) {
     return r;
 }
 
-// canonical prefixes of n digits in the half layout
-int64_t canon64(int n) { return ((int64_t(1) << (2 * n)) + (int64_t(1) << n)) >> 1; }
+// canonical prefixes of n digits in the half layout: ((M^2)^n + M^n) / 2
+int64_t canon64(int M, int n) { return (ipow64((int64_t)M * M, n) + ipow64(M, n)) >> 1; }
 
 // tiles of instance (L, N) at step n for the given tile size
 unsigned tiles_at(int M2, int L, int64_t N, int n, int te, int read_nin, bool herm) {
     if (n < 1 || n > N) return 0;
     int64_t units;
     if (herm) {
-        if (n < L && n < N) units = 4 * canon64(n - 1);         // growth: stored input entries
-        else if (n < N) units = canon64(L - 1);                 // step: canonical prefixes
-        else units = canon64(read_nin - 1);                     // readout: canonical prefixes
+        const int M = M2 == 4 ? 2 : 3;
+        if (n < L && n < N) units = M2 * canon64(M, n - 1);     // growth: stored input entries
+        else if (n < N) units = canon64(M, L - 1);              // step: canonical prefixes
+        else units = canon64(M, read_nin - 1);                  // readout: canonical prefixes
     } else {
         if (n < L && n < N) units = ipow64(M2, n);              // growth: input entries
         else if (n < N) units = ipow64(M2, L - 1);              // step: fibers
@@ -364,9 +365,6 @@ extern "C" quapi_status quapi_propagate_batch(int n, quapi_ctx* const* ctxs, con
         }
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return record_error(nullptr, QUAPI_ERR_ARG, "batch: a context appears twice");
-        if (ctx_half_layout(ctxs[i]) && M == 3)
-            return record_error(nullptr, QUAPI_ERR_UNSUPPORTED,
-                                "batch: the Hermitian half layout of M = 3 runs through quapi_propagate only");
         if (ctx_half_layout(ctxs[i])) {  // the half layout stores one of each conjugate pair: rho0 = rho0^dagger
             const double* r0 = rho0s[i];
             for (int r = 0; r < M; ++r)

@@ -349,6 +349,140 @@ __device__ void herm_grow_tile(const OpRef& op, const void* in, void* outv, int 
     }
 }
 
+// ---- Hermitian half layout, M = 3, for tiled instances ------------------------------------
+// Positions, rows and conjugate partners as in the single-instance M = 3 half-layout kernels: one
+// canonical prefix f gives all nine rows of its fiber; rows 1, 2, 5 go to their plain blocks at f,
+// rows 3, 6, 7 (conjugated) to the same blocks at conj f, rows 0, 4, 8 to the fiber of (x, f / 9).
+// Each position of the tile is decoded on its own (base-9 walk).
+
+template <int FORM, int FPT>
+__device__ void herm3_step_tile(const OpRef& op, const void* in, void* outv, int np, int64_t tile_base) {
+    using Elem = typename Form<FORM>::Elem;
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    Elem* out = reinterpret_cast<Elem*>(outv);
+    const uint32_t npre = half3_count(np);
+    const uint32_t P1 = pow9(np);
+    const uint32_t sbase = (np >= 1) ? P1 / 3u : 0u;
+    const uint32_t cnh = (np >= 1) ? half3_count(np - 1) : 0u;
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t c = (uint32_t)tile_base + u * kBThreads + threadIdx.x;
+        if (c >= npre) break;
+        uint32_t f, h;
+        bool sc, shc;
+        half3_decode_pair(c, np, f, sc, h, shc);
+        Elem a[9], o[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a[q] = ld_l2(A + 9ull * c + q);
+        step_fiber_dispatch<3, FORM>(op, a, f, o);
+        if (np == 0) {
+#pragma unroll
+            for (int x = 0; x < 9; ++x) out[x] = o[x];
+            continue;
+        }
+        const uint32_t f0 = f % 9u, e0 = 9u * (sbase + h) + f0, e1 = e0 - f0 + conj3(f0);
+        out[f] = o[1];
+        out[P1 + f] = o[2];
+        out[2u * P1 + f] = o[5];
+        out[e0] = o[0];
+        out[e0 + 9u * cnh] = o[4];
+        out[e0 + 18u * cnh] = o[8];
+        if (!sc) {
+            const uint32_t fb = conj_digits3(f, np);
+            out[fb] = conjv(o[3]);
+            out[P1 + fb] = conjv(o[6]);
+            out[2u * P1 + fb] = conjv(o[7]);
+            if (shc) {  // the fiber of a self-conjugate (x, f / 9) keeps every last digit
+                out[e1] = conjv(o[0]);
+                out[e1 + 9u * cnh] = conjv(o[4]);
+                out[e1 + 18u * cnh] = conjv(o[8]);
+            }
+        }
+    }
+}
+
+// Readout contributions of positions c = base + u * kBThreads + threadIdx.x: rows 1, 2, 5 over f and its
+// conjugate (r_x + conj r_conj(x)), twice the real part of rows 0, 4, 8; rows 3, 6, 7 of rho are the
+// conjugates of rows 1, 2, 5 and are filled in by the caller.
+template <int FORM, int FPT>
+__device__ void herm3_read_tile(const OpRef& op, const void* in, int np, int64_t tile_base, Acc<FORM> (&acc)[9]) {
+    using Elem = typename Form<FORM>::Elem;
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    const uint32_t npre = half3_count(np);
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t c = (uint32_t)tile_base + u * kBThreads + threadIdx.x;
+        if (c >= npre) break;
+        uint32_t f;
+        bool sc;
+        half3_decode(c, np, f, sc);
+        Elem a[9], r[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) a[q] = ld_l2(A + 9ull * c + q);
+        step_fiber_dispatch<3, FORM>(op, a, f, r);
+        acc[1].add(r[1]);
+        acc[2].add(r[2]);
+        acc[5].add(r[5]);
+        if (!sc) {
+            acc[1].add(conjv(r[3]));
+            acc[2].add(conjv(r[6]));
+            acc[5].add(conjv(r[7]));
+            acc[0].add(twice_real(r[0]));
+            acc[4].add(twice_real(r[4]));
+            acc[8].add(twice_real(r[8]));
+        } else {
+            acc[0].add(real_part(r[0]));
+            acc[4].add(real_part(r[4]));
+            acc[8].add(real_part(r[8]));
+        }
+    }
+}
+
+// Growth n_in -> n_in + 1 digits in the M = 3 half layout: stored input entries
+// e = base + u * kBThreads + threadIdx.x (the rules of herm3_grow_kernel).
+template <int FORM, int FPT>
+__device__ void herm3_grow_tile(const OpRef& op, const void* in, void* outv, int n_in, int64_t tile_base) {
+    using Elem = typename Form<FORM>::Elem;
+    const OpTabs<3, FORM> T = tabs_of<3, FORM>(op);
+    const Elem* A = reinterpret_cast<const Elem*>(in);
+    Elem* out = reinterpret_cast<Elem*>(outv);
+    const uint32_t S = pow9(n_in);
+    const uint32_t Cp = half3_count(n_in - 1);
+    const uint32_t sbase = S / 3u;
+    auto Pm = [&](int x, uint32_t idx, Elem w) {
+        uint32_t ih, il;
+        T.split(idx, ih, il);
+        return tab_mul(ldt(T.hi + (int64_t)x * T.hi_size + ih), tab_mul(ldt(T.lo + x * T.lo_size + il), w));
+    };
+#pragma unroll 1
+    for (int u = 0; u < FPT; ++u) {
+        const uint32_t e = (uint32_t)tile_base + u * kBThreads + threadIdx.x;
+        if (e >= 9u * Cp) break;
+        const uint32_t c = e / 9u, d = e % 9u;
+        uint32_t P;
+        bool scP;
+        half3_decode(c, n_in - 1, P, scP);
+        const uint32_t i = P * 9u + d;
+        const Elem v = ld_l2(A + e);
+        const bool dtop = (d == 1u || d == 2u || d == 5u);
+        if (!(scP && !dtop && !self3(d))) {
+            out[i] = Pm(1, i, v);
+            out[S + i] = Pm(2, i, v);
+            out[2u * S + i] = Pm(5, i, v);
+        }
+        if (!scP || dtop) {
+            const uint32_t ib = conj_digits3(i, n_in);
+            const Elem vb = conjv(v);
+            out[ib] = Pm(1, ib, vb);
+            out[S + ib] = Pm(2, ib, vb);
+            out[2u * S + ib] = Pm(5, ib, vb);
+        }
+        out[9u * (sbase + c) + d] = Pm(0, i, v);
+        out[9u * (sbase + Cp + c) + d] = Pm(4, i, v);
+        out[9u * (sbase + 2u * Cp + c) + d] = Pm(8, i, v);
+    }
+}
+
 // One instance, every step in shared memory (resident instances).
 template <int M, int FORM>
 __device__ void run_resident(const BatchInst& I, unsigned char* smem, double2 (*red)[M * M]) {
@@ -482,11 +616,14 @@ __global__ void __launch_bounds__(kBThreads, batch_min_ctas<M, FORM, HO>()) batc
         void* outv = I.buf[n & 1];
         for (unsigned t = t0; t < t1; ++t) {
             const int64_t base = (int64_t)t * TE + (int64_t)threadIdx.x * FPT;
-            const bool herm = HO || ((M == 2) && I.herm);
+            const bool herm = HO || I.herm;
             if (herm && n < I.N) {
                 if constexpr (M == 2) {
                     if (n < I.L) herm_grow_tile<FORM, FPT>(I.grow[n], in, outv, n, (int64_t)t * TE);
                     else herm_step_tile<FORM, FPT>(n == I.L ? I.step_first : I.step, in, outv, I.L - 1, (int64_t)t * TE);
+                } else if constexpr (!HO) {
+                    if (n < I.L) herm3_grow_tile<FORM, FPT>(I.grow[n], in, outv, n, (int64_t)t * TE);
+                    else herm3_step_tile<FORM, FPT>(n == I.L ? I.step_first : I.step, in, outv, I.L - 1, (int64_t)t * TE);
                 }
             } else if (!HO && n < I.L && n < I.N) {
                 int64_t S = 1;
@@ -563,6 +700,7 @@ __global__ void __launch_bounds__(kBThreads, batch_min_ctas<M, FORM, HO>()) batc
                 for (int x = 0; x < M2; ++x) acc[x].init();
                 if (herm) {
                     if constexpr (M == 2) herm_read_tile<FORM, FPT>(I.read, in, I.read.n_in - 1, (int64_t)t * TE, acc);
+                    else if constexpr (!HO) herm3_read_tile<FORM, FPT>(I.read, in, I.read.n_in - 1, (int64_t)t * TE, acc);
                 } else if constexpr (!HO) {
 #pragma unroll
                     for (int u = 0; u < FPT; ++u) {
@@ -579,9 +717,11 @@ __global__ void __launch_bounds__(kBThreads, batch_min_ctas<M, FORM, HO>()) batc
                 }
                 const double2 v = block_rows_sum<M2, FORM>(acc, red);
                 if (threadIdx.x < M2) {
-                    // half layout: row 2 is the conjugate of row 1 (thread 2 holds an empty sum)
-                    if (!(herm && threadIdx.x == 2)) I.partial[(int64_t)t * M2 + threadIdx.x] = v;
-                    if (herm && threadIdx.x == 1) I.partial[(int64_t)t * M2 + 2] = make_double2(v.x, -v.y);
+                    // half layout: the rows (a, b) with a > b are the conjugates of the rows (b, a) (their
+                    // threads hold empty sums)
+                    const int x = threadIdx.x, xa = x / M, xb = x % M;
+                    if (!(herm && xa > xb)) I.partial[(int64_t)t * M2 + x] = v;
+                    if (herm && xa < xb) I.partial[(int64_t)t * M2 + xb * M + xa] = make_double2(v.x, -v.y);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) {

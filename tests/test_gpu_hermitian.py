@@ -161,12 +161,12 @@ def test_half_layout_checkpoint_and_rejections(q):
     finally:
         q.quapi_destroy(c1)
         q.quapi_destroy(c2)
-    # the three-level half layout is set up, but the batched form does not take it
+    # the three-level half layout needs a Hermitian rho0 too (batched form)
     c3 = q.quapi_setup([-1, 0, 1], np.eye(3), "ohmic_exp", 0.1, 5.0, 1.0, 0.1, 3, q.quapi_opts_init(hermitian=1))
     try:
         with pytest.raises(q.QuapiError) as e:
-            q.quapi_propagate_batch([c3], [np.diag([1.0, 0.0, 0.0])], [4], M=3)
-        assert e.value.status == q.QUAPI_ERR_UNSUPPORTED
+            q.quapi_propagate_batch([c3], [np.array([[1, 1j, 0], [1j, 0, 0], [0, 0, 0]])], [4], M=3)
+        assert e.value.status == q.QUAPI_ERR_ARG
     finally:
         q.quapi_destroy(c3)
 

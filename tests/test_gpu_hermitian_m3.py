@@ -134,12 +134,25 @@ def test_m3_half_layout_checkpoint_round_trip(q):
     assert np.abs(resumed - whole).max() <= 1e-13
 
 
-def test_m3_half_layout_batched_is_unsupported(q):
-    p = wl.three_level_L8()
-    c = q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, 3, q.quapi_opts_init(hermitian=1))
+@pytest.mark.parametrize("prec", [64, 32, 48])
+def test_m3_half_layout_batched_against_oracle(q, prec):
+    """Three-level instances in the half layout through the batched launch: memory lengths 2..6 (the
+    smallest stay in shared memory), final steps in the growth phase, at the first summing step and
+    beyond; each rho(t_N) against the oracle."""
+    probs, Ns = [], [5, 2, 9, 4, 14, 6, 11]
+    for i, L in enumerate([2, 3, 4, 4, 5, 6, 6]):
+        p = wl.three_level_L8()
+        p.L = L
+        p.H = wl.random_hermitian(3, 70 + i)
+        probs.append(p)
+    ctxs = [q.quapi_setup(p.s, p.H, p.jkind, p.ja, p.wc, p.beta, p.dt, p.L,
+                          q.quapi_opts_init(precision=prec, hermitian=1)) for p in probs]
     try:
-        with pytest.raises(q.QuapiError) as e:
-            q.quapi_propagate_batch([c], [p.rho0], [5], M=3)
-        assert e.value.status == q.QUAPI_ERR_UNSUPPORTED
+        for rep in range(2):  # the second call replays the captured graph
+            got = q.quapi_propagate_batch(ctxs, [p.rho0 for p in probs], Ns, M=3)
+            for p, N, r in zip(probs, Ns, got):
+                want = oracle.propagate(p.s, p.H, Spectral(p.jkind, p.ja, p.wc), p.beta, p.dt, p.L, p.rho0, [N])[N]
+                assert np.abs(r - want).max() <= TOL[prec], (p.L, N, rep)
     finally:
-        q.quapi_destroy(c)
+        for c in ctxs:
+            q.quapi_destroy(c)
