@@ -75,7 +75,10 @@ typedef struct {
 enum {
     QUAPI_FP64 = 64,  /* tensor stored and propagated in complex double */
     QUAPI_FP32 = 32,  /* complex float storage and products; double-float tables,
-                         compensated index sums, FP64 eta / K / readout */
+                         compensated index sums (FP32 products of the tables' hi
+                         floats inside the sums once K sits in the hi table; the
+                         factors that carry K keep both floats), FP64 eta / K /
+                         readout */
     QUAPI_DF64 = 48   /* FP64-equivalent form on the FP32 pipes: each entry stored as a
                          double-float pair (hi + lo floats, 16 B per complex entry, ~48-bit
                          significands), triple-float tables holding the FP64 values exactly,

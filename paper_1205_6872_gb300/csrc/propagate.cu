@@ -12,7 +12,7 @@
 //
 // Readout (Sec. IV, allPoints / justFinalPoint): rho(t_n)[x] is the same
 // product with the end-point tables, summed over f instead of stored; each CTA
-// writes its partial sums (FP64) and rho_reduce_kernel adds them in CTA order.
+// writes its partial sums (FP64) and rho_reduce_kernel adds them in a fixed order.
 //
 // Memory access: every thread owns FPT consecutive fibers (FP32 with M = 2: 2, so
 // that its 2 outputs per row form one 16-byte store; otherwise 1); a warp reads one
@@ -184,20 +184,22 @@ template <> struct RhoAcc<QUAPI_DF64> {
     }
 };
 
-// Sum over the oldest index with the summed-digit table (compensated in FP32).
-template <int M2>
+// Sum over the oldest index with the summed-digit table.  FP32: Kahan-compensated, with FP32 products
+// of the table's hi float when HIP (the fast path: no summed-index entry carries K), else products with
+// both floats of the entry.  HIP changes nothing in the other forms.
+template <int M2, bool HIP = false>
 __device__ __forceinline__ double2 row_sum(const double2* __restrict__ isum_row, const double2 (&a)[M2]) {
     double2 s = cmul(isum_row[0], a[0]);
 #pragma unroll
     for (int q = 1; q < M2; ++q) s = cfma(isum_row[q], a[q], s);
     return s;
 }
-template <int M2>
+template <int M2, bool HIP = false>
 __device__ __forceinline__ kahan32 row_sum(const ff2* __restrict__ isum_row, const float2 (&a)[M2]) {
     kahan32 acc;
-    acc.init(ffmul(isum_row[0], a[0]));
+    acc.init(HIP ? fmul_hi(isum_row[0], a[0]) : ffmul(isum_row[0], a[0]));
 #pragma unroll
-    for (int q = 1; q < M2; ++q) acc.add(ffmul(isum_row[q], a[q]));
+    for (int q = 1; q < M2; ++q) acc.add(HIP ? fmul_hi(isum_row[q], a[q]) : ffmul(isum_row[q], a[q]));
     return acc;
 }
 template <int M2> __device__ __forceinline__ double2 plain_sum(const double2 (&a)[M2]) {
@@ -216,7 +218,7 @@ template <int M2> __device__ __forceinline__ kahan32 plain_sum(const float2 (&a)
 
 // DF64 sums over the oldest index: started from the first term and left unrenormalised, because
 // every caller multiplies them by a table entry next (the product takes the pair as it is)
-template <int M2>
+template <int M2, bool HIP = false>
 __device__ __forceinline__ df2 row_sum(const tf2* __restrict__ isum_row, const df2 (&a)[M2]) {
     dfacc acc;
     acc.init_prod(isum_row[0], a[0]);
@@ -310,12 +312,13 @@ template <int FORM, bool DIAG> __host__ __device__ constexpr bool herm_row1() {
     return DIAG && !herm_fold<FORM>() && !FormT<FORM>::kFoldLo;
 }
 
-// sum_old W1[old][fl] * a[old]: FP32 Kahan-compensated, DF64 exact products added with TwoSum
+// sum_old W1[old][fl] * a[old] (fast path only): FP32 products of the hi float, Kahan-compensated;
+// DF64 exact products added with TwoSum
 __device__ __forceinline__ kahan32 fold_sum(const FoldRow<QUAPI_FP32>& W, uint32_t fl, const float2 (&a)[4]) {
     kahan32 acc;
-    acc.init(ffmul(W.at(0, fl), a[0]));
+    acc.init(fmul_hi(W.at(0, fl), a[0]));
 #pragma unroll
-    for (int q = 1; q < 4; ++q) acc.add(ffmul(W.at(q, fl), a[q]));
+    for (int q = 1; q < 4; ++q) acc.add(fmul_hi(W.at(q, fl), a[q]));
     return acc;
 }
 // DF64: left unrenormalised (it is multiplied by hi next)
@@ -514,12 +517,12 @@ __device__ __forceinline__ void process_fibers(const StepTables<M, FORM>& T,
                     }
                 } else {
                     if (WRITE) {
-                        auto S = row_sum<M2>(T.isum + x * M2, a[u]);
+                        auto S = row_sum<M2, DIAG>(T.isum + x * M2, a[u]);
                         vout[u] = apply_p(same ? h0 : T.hi[(int64_t)x * T.hi_size + fhi[u]],
                                           T.lo[x * T.lo_size + flo[u]], S);
                     }
                     if (READ) {
-                        auto Se = row_sum<M2>(T.isume + x * M2, a[u]);
+                        auto Se = row_sum<M2, DIAG>(T.isume + x * M2, a[u]);
                         vread[u] = apply_p(same ? he0 : T.hie[(int64_t)x * T.hi_size + fhi[u]],
                                            T.loe[x * T.lo_size + flo[u]], Se);
                     }
@@ -855,16 +858,16 @@ __device__ __forceinline__ void herm_rows(const StepTables<2, FORM>& T, const ty
             if constexpr (END) {  // the readout's folded row-1 table
                 o[1] = apply_hi(hi[T.hi_size + (f >> 8)], fold_sum(T.w1e, f & 255u, a));
             } else {  // lo_size = 256 on the fast path
-                o[1] = apply_p(hi[T.hi_size + (f >> 8)], T.r1[4 + (f & 255u)], row_sum<4>(T.r1, a));
+                o[1] = apply_p(hi[T.hi_size + (f >> 8)], T.r1[4 + (f & 255u)], row_sum<4, true>(T.r1, a));
             }
             return;
         }
         if (ONLY1) {
         } else {
-            o[0] = apply_p(hi[fh], lo[fl], row_sum<4>(isum, a));
-            o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4>(isum + 12, a));
+            o[0] = apply_p(hi[fh], lo[fl], row_sum<4, DIAG>(isum, a));
+            o[3] = apply_p(hi[3 * T.hi_size + fh], lo[3 * T.lo_size + fl], row_sum<4, DIAG>(isum + 12, a));
         }
-        o[1] = apply_p(hi[T.hi_size + fh], lo[T.lo_size + fl], row_sum<4>(isum + 4, a));
+        o[1] = apply_p(hi[T.hi_size + fh], lo[T.lo_size + fl], row_sum<4, DIAG>(isum + 4, a));
     }
 }
 
@@ -1106,14 +1109,14 @@ __device__ __forceinline__ void load_fiber9(const typename FormT<FORM>::Elem* __
 
 // The sum over the oldest index of row x, multiplied by lo (FP64: the folded lo (x) isum sum): the row
 // is then hi[x][fh] times it (step tables, or the readout's with END).
-template <int FORM, bool END>
+template <int FORM, bool END, bool DIAG>
 __device__ __forceinline__ auto lo_sum9(const StepTables<3, FORM>& T, const typename FormT<FORM>::Elem (&a)[9], int x,
                                         uint32_t fl) {
     if constexpr (FormT<FORM>::kFoldLo) {
         const auto* w = END ? T.we : T.w;  // lo (x) isum
         return row_sum<9>(w + ((int64_t)x * T.lo_size + fl) * 9, a);
     } else if constexpr (FORM == QUAPI_FP32) {
-        const kahan32 S = row_sum<9>((END ? T.isume : T.isum) + x * 9, a);
+        const kahan32 S = row_sum<9, DIAG>((END ? T.isume : T.isum) + x * 9, a);
         return ffmul2((END ? T.loe : T.lo)[x * T.lo_size + fl], S.s, S.c);
     } else {
         return tfmul((END ? T.loe : T.lo)[x * T.lo_size + fl], row_sum<9>((END ? T.isume : T.isum) + x * 9, a));
@@ -1141,7 +1144,7 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
         const uint32_t f0 = f % 9u;
         const uint32_t e0 = 9u * (sbase + h) + f0;  // rows 0, 4, 8: their fibers are C3(np - 1) prefixes apart
         const uint32_t e1 = e0 - f0 + conj3(f0);
-        decltype(lo_sum9<FORM, false>(T, a, 0, fl)) ls;
+        decltype(lo_sum9<FORM, false, DIAG>(T, a, 0, fl)) ls;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int x = order[k];
@@ -1150,7 +1153,7 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
             if (DIAG && is_diag<3>(x)) {
                 v = apply_hi(hx, Sd);
             } else {
-                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, false>(T, a, x, fl);
+                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, false, DIAG>(T, a, x, fl);
                 v = tmul(hx, ls);
             }
             if (np == 0) {  // one-digit output: every point stored
@@ -1169,7 +1172,7 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
         }
     }
     if (READ) {
-        decltype(lo_sum9<FORM, true>(T, a, 0, fl)) ls;
+        decltype(lo_sum9<FORM, true, DIAG>(T, a, 0, fl)) ls;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             const int x = order[k];
@@ -1178,7 +1181,7 @@ __device__ __forceinline__ void herm3_fiber(const StepTables<3, FORM>& T, const 
             if (DIAG && is_diag<3>(x)) {
                 r = apply_hi(hx, Sd);
             } else {
-                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, true>(T, a, x, fl);
+                if (!(SHARE && (x == 5 || x == 7))) ls = lo_sum9<FORM, true, DIAG>(T, a, x, fl);
                 r = tmul(hx, ls);
             }
             if (x == 1 || x == 2 || x == 5) {
@@ -1397,13 +1400,26 @@ __global__ void __launch_bounds__(kThreads) grow_kernel(const void* __restrict__
     }
 }
 
-__global__ void rho_reduce_kernel(const double2* __restrict__ partial, int nparts, int M2,
-                                  double2* __restrict__ rho_out) {
-    int x = threadIdx.x;
-    if (x >= M2) return;
+// rho_out[x] = the sum of the nparts per-CTA partials of entry x (stored [part][x]), in a fixed order
+// that does not depend on timing: thread t of the 32 M2 adds, in turn, the partials j, j + 32, j + 64,
+// ... of entry x = t % M2 (j = t / M2; consecutive threads read consecutive partials), then thread x
+// adds the 32 sums of its entry in the order j = 0..31.
+constexpr int kReduceLanes = 32;
+__global__ void __launch_bounds__(kReduceLanes * 9) rho_reduce_kernel(const double2* __restrict__ partial,
+                                                                       int nparts, int M2,
+                                                                       double2* __restrict__ rho_out) {
+    __shared__ double2 sums[kReduceLanes * 9];
+    const int t = threadIdx.x, x = t % M2, j = t / M2;
     double2 v = make_double2(0.0, 0.0);
-    for (int b = 0; b < nparts; ++b) v = cadd(v, partial[(int64_t)b * M2 + x]);
-    rho_out[x] = v;
+#pragma unroll 4
+    for (int b = j; b < nparts; b += kReduceLanes) v = cadd(v, partial[(int64_t)b * M2 + x]);
+    sums[t] = v;
+    __syncthreads();
+    if (t < M2) {
+        double2 r = sums[t];
+        for (int k = 1; k < kReduceLanes; ++k) r = cadd(r, sums[k * M2 + t]);
+        rho_out[t] = r;
+    }
 }
 
 template <int M, int FORM, bool W, bool R, bool D>
@@ -1702,7 +1718,8 @@ cudaError_t launch_grow(int M, int form, const void* A_in, void* A_out, int64_t 
 }
 
 cudaError_t launch_rho_reduce(const double2* partial, int nparts, int M2, double2* rho_out, cudaStream_t st) {
-    rho_reduce_kernel<<<1, 32, 0, st>>>(partial, nparts, M2, rho_out);
+    if (M2 < 1 || M2 > 9) return cudaErrorInvalidValue;
+    rho_reduce_kernel<<<1, kReduceLanes * M2, 0, st>>>(partial, nparts, M2, rho_out);
     count_launch();
     return cudaGetLastError();
 }

@@ -49,6 +49,14 @@ __device__ __forceinline__ float2 ffmul(const ff2& T, float2 v) {
     return make_float2(re, im);
 }
 
+// T * v with the table's hi float alone: one rounded FP32 complex product.  The summed-index sums of
+// the FP32 form take their products this way on the fast path, where K sits in the hi table and no
+// summed-index entry carries it (its lo float would only refine a factor close to 1 below the rounding
+// of the stored FP32 data; K's own rounding would leak trace, so K's tables keep both floats).
+__device__ __forceinline__ float2 fmul_hi(const ff2& T, float2 v) {
+    return make_float2(fmaf(T.hr, v.x, -T.hi * v.y), fmaf(T.hr, v.y, T.hi * v.x));
+}
+
 // (T.hi + T.lo) * (s + c) where (s, c) is a compensated FP32 value (|c| << |s|).
 __device__ __forceinline__ float2 ffmul2(const ff2& T, float2 s, float2 c) {
     float re = fmaf(T.lr, s.x, -T.li * s.y);
