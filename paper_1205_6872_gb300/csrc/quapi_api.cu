@@ -90,6 +90,22 @@ struct quapi_ctx {
     int eq_spaced = 0;           // M = 3 with s_1 - s_0 = s_2 - s_1 (exactly, in FP64)
     uint64_t wait_ns = 2000000000ull;  // limit of the step kernels' device-side waits
     uint32_t fault_tx = 0;       // host-side fault injection into the TMA step (testing)
+    // A whole propagation captured as a CUDA graph and replayed when the same call (rho0 buffer, rho
+    // slots, step list) comes again: one graph launch instead of one host launch sequence per step
+    // (which bounds small, L2-resident tensors).  The first call with new arguments runs directly and
+    // only records them; the second captures on a private stream and replays from then on.
+    struct PropGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cap = nullptr;     // the capture stream (non-blocking, created on first use)
+        bool ready = false;             // exec holds the propagation of the recorded arguments
+        const void* rho0 = nullptr;
+        const void* slots = nullptr;
+        std::vector<int64_t> steps;
+        int64_t state_n = -1;           // the host bookkeeping the captured propagation leaves
+        int state_buf = 0;
+        uint64_t launches = 0;          // kernels in the graph
+    } graph;
+    bool graphs = true;             // QUAPI_GRAPH=0 turns the replay off
     std::vector<OpPlan> grow_ops;   // index n = 1..L-1
     std::vector<OpPlan> read_ops;   // index N = 1..L
     OpPlan step_first, step_steady, read_steady;
@@ -345,6 +361,7 @@ quapi_status setup_impl(const double* s, int M, const double* H, const quapi_spe
     SCHECK(cudaMalloc(&c->d_err, sizeof(int)), "cudaMalloc(error flag)");
     SCHECK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st), "clear error flag");
     if (const char* v = std::getenv("QUAPI_TMA")) c->use_tma = std::atoi(v) != 0;
+    if (const char* v = std::getenv("QUAPI_GRAPH")) c->graphs = std::atoi(v) != 0;
     if (const char* v = std::getenv("QUAPI_WAIT_MS")) {
         const double ms = std::atof(v);
         if (ms > 0) c->wait_ns = (uint64_t)(ms * 1e6);
@@ -685,6 +702,60 @@ quapi_status propagate_enqueue(quapi_ctx* c, const double2* rho0_dev, const int6
     return run_steps(c, 0, 0, steps, nsteps, next, slots);
 }
 
+// propagate_enqueue through the context's propagation graph (see quapi_ctx::PropGraph).  A capture that
+// fails (a launch that stream capture does not allow) turns the replay off for the context and runs the
+// propagation directly.
+quapi_status propagate_graphed(quapi_ctx* c, const double2* rho0_dev, const int64_t* steps, int nsteps,
+                               double2* slots) {
+    auto& g = c->graph;
+    const bool same = g.rho0 == rho0_dev && g.slots == slots && g.steps.size() == (size_t)nsteps &&
+                      std::equal(steps, steps + nsteps, g.steps.begin());
+    if (!c->graphs || !same) {
+        g.ready = false;
+        g.rho0 = rho0_dev;
+        g.slots = slots;
+        g.steps.assign(steps, steps + nsteps);
+        return propagate_enqueue(c, rho0_dev, steps, nsteps, slots);
+    }
+    if (!g.ready) {
+        if ((!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) ||
+            cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graphs = false;
+            return propagate_enqueue(c, rho0_dev, steps, nsteps, slots);
+        }
+        cudaStream_t user = c->st;
+        c->st = g.cap;
+        const uint64_t l0 = launches_so_far();
+        const quapi_status s = propagate_enqueue(c, rho0_dev, steps, nsteps, slots);
+        c->st = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
+        cudaGraphExec_t exec = nullptr;
+        const bool ok = s == QUAPI_OK && e == cudaSuccess && graph &&
+                        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();  // a refused capture leaves no sticky error
+            c->graphs = false;
+            return propagate_enqueue(c, rho0_dev, steps, nsteps, slots);
+        }
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = exec;
+        g.launches = launches_so_far() - l0;
+        g.state_n = c->state_n;
+        g.state_buf = c->state_buf;
+        g.ready = true;
+        QCHECK(c, cudaGraphLaunch(g.exec, c->st), "graph launch");
+        return QUAPI_OK;  // the captured launches were counted as they were recorded
+    }
+    QCHECK(c, cudaGraphLaunch(g.exec, c->st), "graph launch");
+    count_launch(g.launches);
+    c->state_n = g.state_n;
+    c->state_buf = g.state_buf;
+    return QUAPI_OK;
+}
+
 int64_t state_elements(const quapi_ctx* c, int64_t n) {
     const int d = (int)std::min<int64_t>(n + 1, c->L);
     return c->herm ? half_entries(c->M, d) : ipow(c->M2, d);
@@ -846,7 +917,7 @@ quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const in
         return fail(c, QUAPI_ERR_ARG, "device buffers must be 16-byte aligned");
     quapi_status s = check_steps(c, steps, nsteps);
     if (s != QUAPI_OK) return s;
-    return propagate_enqueue(c, static_cast<const double2*>(rho0_dev), steps, nsteps,
+    return propagate_graphed(c, static_cast<const double2*>(rho0_dev), steps, nsteps,
                              static_cast<double2*>(rho_out_dev));
 }
 
@@ -867,7 +938,7 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
     s = ensure_slots(c, nsteps);
     if (s != QUAPI_OK) return s;
     QCHECK(c, cudaMemcpyAsync(c->d_rho0, rho0, sizeof(double2) * c->M2, cudaMemcpyHostToDevice, c->st), "copy rho0");
-    s = propagate_enqueue(c, c->d_rho0, steps, nsteps, c->d_slots);
+    s = propagate_graphed(c, c->d_rho0, steps, nsteps, c->d_slots);
     if (s != QUAPI_OK) return s;
     QCHECK(c, cudaMemcpyAsync(rho_out, c->d_slots, sizeof(double2) * c->M2 * (size_t)nsteps, cudaMemcpyDeviceToHost,
                               c->st),
@@ -977,6 +1048,8 @@ void quapi_destroy(quapi_ctx* c) {
     cudaFree(c->d_tables);
     cudaFree(c->d_partial);
     cudaFree(c->d_err);
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    if (c->graph.cap) cudaStreamDestroy(c->graph.cap);
     delete c;
 }
 
