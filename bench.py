@@ -274,11 +274,12 @@ def time_form(q, torch, p, precision, steps, warmup, stream, world, sampler=None
                 for r in range(reps):
                     src, dst = (A, B) if r % 2 == 0 else (B, A)
                     q.quapi_step_device(ctx, p.L + 1, src, dst, None)
-            for _ in range(2):
+            with torch.cuda.stream(stream):  # replay() launches into the current stream
+                for _ in range(2):
+                    graph.replay()
+                k0.record(stream)
                 graph.replay()
-            k0.record(stream)
-            graph.replay()
-            k1.record(stream)
+                k1.record(stream)
             k1.synchronize()
             kern_ms = k0.elapsed_time(k1) / reps
             del graph
