@@ -185,7 +185,16 @@ quapi_status quapi_propagate(quapi_ctx* c, const double* rho0, const int64_t* st
 /* As quapi_propagate with rho0 and rho_out in device memory (complex double,
  * 16-byte aligned), enqueued on the context's stream without a host
  * synchronisation.  steps is a host array.  Errors as quapi_propagate, and
- * QUAPI_ERR_ARG for a device pointer that is not 16-byte aligned. */
+ * QUAPI_ERR_ARG for a device pointer that is not 16-byte aligned.
+ *
+ * Both propagate calls replay a CUDA graph when called again with the same
+ * arguments: the second call with a given (rho0 buffer, rho_out buffer, step
+ * list) -- for quapi_propagate, the context's own device copies -- captures the
+ * whole propagation on a private stream and launches it into the context's
+ * stream; later calls with the same arguments launch that graph, which reads
+ * the buffers' current contents.  Results are bitwise those of direct
+ * launches.  The environment variable QUAPI_GRAPH=0, read at set-up, turns the
+ * replay off for the context. */
 quapi_status quapi_propagate_device(quapi_ctx* c, const void* rho0_dev, const int64_t* steps,
                                     int nsteps, void* rho_out_dev);
 
