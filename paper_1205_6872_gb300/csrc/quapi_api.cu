@@ -31,6 +31,7 @@ using namespace quapi;
 namespace quapi {
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace quapi
 
@@ -737,6 +738,7 @@ quapi_status propagate_graphed(quapi_ctx* c, const double2* rho0_dev, const int6
         if (graph) cudaGraphDestroy(graph);
         if (!ok) {
             cudaGetLastError();  // a refused capture leaves no sticky error
+            uncount_launches(launches_so_far() - l0);  // recorded, never run: the direct run counts its own
             c->graphs = false;
             return propagate_enqueue(c, rho0_dev, steps, nsteps, slots);
         }
