@@ -46,7 +46,7 @@ typedef enum {
     QUAPI_ERR_ARG = 1,          /* invalid argument (non-Hermitian H, M not 2 or 3, dt <= 0, ...) */
     QUAPI_ERR_OOM = 2,          /* device memory (or the caller's workspace) too small */
     QUAPI_ERR_CUDA = 3,         /* a CUDA runtime/driver call failed */
-    QUAPI_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up (batched kernel) */
+    QUAPI_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up (batched kernel, TMA-staged step) */
     QUAPI_ERR_UNSUPPORTED = 5   /* valid request this build does not implement */
 } quapi_status;
 
