@@ -102,9 +102,9 @@ def test_decode_position_and_conjugation(table, n):
 
 @pytest.mark.parametrize("n", range(2, NMAX + 1))
 def test_run_property(table, n):
-    """run(c) >= 1 exactly at the positions in a plain block of a canonical top digit at level >= 2; inside
-    a run the next position holds the next plain prefix, its run is one shorter, and the canonical position
-    of its last-digit-free prefix advances when the last digit wraps (f % 9 = 8 -> 0)."""
+    """run(c) is 0 at self-conjugate prefixes; inside a run the next position holds the next plain prefix,
+    its run is one shorter, and the canonical position of its last-digit-free prefix advances when the last
+    digit wraps (f % 9 = 8 -> 0)."""
     _, data = table
     t = data[data[:, 0] == n]
     f, h, run, sc = t[:, 8], t[:, 10], t[:, 12], t[:, 9]
